@@ -1,0 +1,179 @@
+"""ctypes wrapper around the plain C oracle in ``polar_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The product path never
+imports this module, and this module imports nothing from the product package.
+
+Paper: arXiv 1505.04979.  The C file cites the section / equation each
+function follows (Sec. II code construction and encoder, Eq. (1) PE update,
+Eqs. (2)-(4) CSFG check, Sec. IV computation count).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "polar_oracle.c")
+_LIB = os.path.join(_HERE, "libpolar_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STOP_NONE = 0
+STOP_GMATRIX = 1
+FREEZE_OFF = 0
+FREEZE_CSFG = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over codewords, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        f32p = ctypes.POINTER(ctypes.c_float)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        ci, cd = ctypes.c_int, ctypes.c_double
+        lib.orc_bec_lnz.argtypes = [ci, cd, f64p, f64p]
+        lib.orc_bec_frozen.argtypes = [ci, ci, cd, u8p]
+        lib.orc_encode.argtypes = [ci, u8p, u8p]
+        lib.orc_csfg_check_ext.argtypes = [ci, f64p, u8p, u8p, u8p]
+        lib.orc_decode.argtypes = [ci, u8p, f32p, ci, cd, ci, ci, ci, u8p, i32p, i64p, f64p,
+                                   f64p, f64p, i32p, i64p]
+        lib.orc_decode_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, ci, u8p, i32p, i64p,
+                                         f64p]
+        lib.orc_max_threads.argtypes = []
+        for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
+                   "orc_decode_batch", "orc_max_threads"):
+            getattr(lib, fn).restype = ci
+        _lib = lib
+        return lib
+
+
+def _p(arr, ctype):
+    if arr is None:
+        return None
+    return arr.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def bec_lnz(N: int, z0: float = 0.5):
+    """(ln z, ln(1-z)) of the N synthetic channels of a BEC(z0) (Sec. II)."""
+    a = np.zeros(N, np.float64)
+    b = np.zeros(N, np.float64)
+    _check(_load().orc_bec_lnz(N, z0, _p(a, ctypes.c_double), _p(b, ctypes.c_double)), "bec_lnz")
+    return a, b
+
+
+def bec_frozen(N: int, K: int, z0: float = 0.5) -> np.ndarray:
+    """Frozen mask (1 = frozen) of the (N, K) code: the N-K largest z (Sec. II)."""
+    out = np.zeros(N, np.uint8)
+    _check(_load().orc_bec_frozen(N, K, z0, _p(out, ctypes.c_uint8)), "bec_frozen")
+    return out
+
+
+def encode(u: np.ndarray) -> np.ndarray:
+    """x = u F^{(x)m} over GF(2) (Sec. II); u is [N] or [batch, N]."""
+    u = np.ascontiguousarray(u, dtype=np.uint8)
+    flat = u.reshape(-1, u.shape[-1])
+    N = flat.shape[1]
+    out = np.zeros_like(flat)
+    lib = _load()
+    for r in range(flat.shape[0]):
+        row_in = np.ascontiguousarray(flat[r])
+        row_out = np.zeros(N, np.uint8)
+        _check(lib.orc_encode(N, _p(row_in, ctypes.c_uint8), _p(row_out, ctypes.c_uint8)), "encode")
+        out[r] = row_out
+    return out.reshape(u.shape)
+
+
+def csfg_check(R: np.ndarray, frozen_sub: np.ndarray):
+    """Eqs. (2)-(4) on one CSFG: returns (passes, x_hat, u_hat)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    fz = np.ascontiguousarray(frozen_sub, dtype=np.uint8)
+    S = R.shape[0]
+    xh = np.zeros(S, np.uint8)
+    uh = np.zeros(S, np.uint8)
+    rc = _load().orc_csfg_check_ext(S, _p(R, ctypes.c_double), _p(fz, ctypes.c_uint8),
+                                     _p(xh, ctypes.c_uint8), _p(uh, ctypes.c_uint8))
+    if rc < 0:
+        _check(rc, "csfg_check")
+    return bool(rc), xh, uh
+
+
+def decode(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE,
+           freeze: int = FREEZE_OFF, fp32: bool = False, trace: bool = False) -> dict:
+    """Decode one codeword (Eq. (1) sweep, G-matrix stop, CSFG freezing).
+
+    Returns a dict with u_hat, iters, pe, margin and, when ``trace`` is set,
+    the per-iteration L / R planes ([iters, m+1, N]), covered-prefix lengths P
+    and per-iteration PE counts.
+    """
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    N = frozen.shape[0]
+    m = N.bit_length() - 1
+    u_hat = np.zeros(N, np.uint8)
+    iters = np.zeros(1, np.int32)
+    pe = np.zeros(1, np.int64)
+    margin = np.zeros(1, np.float64)
+    tl = tr = tp = tpe = None
+    if trace:
+        tl = np.full((max_iter, m + 1, N), np.nan, np.float64)
+        tr = np.full((max_iter, m + 1, N), np.nan, np.float64)
+        tp = np.full(max_iter, -1, np.int32)
+        tpe = np.zeros(max_iter, np.int64)
+    rc = _load().orc_decode(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), max_iter, alpha, stop,
+                            freeze, 1 if fp32 else 0, _p(u_hat, ctypes.c_uint8), _p(iters, ctypes.c_int32),
+                            _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double), _p(tl, ctypes.c_double),
+                            _p(tr, ctypes.c_double), _p(tp, ctypes.c_int32), _p(tpe, ctypes.c_int64))
+    _check(rc, "decode")
+    out = {"u_hat": u_hat, "iters": int(iters[0]), "pe": int(pe[0]), "margin": float(margin[0])}
+    if trace:
+        n = out["iters"]
+        out.update(L=tl[:n], R=tr[:n], P=tp[:n], pe_iter=tpe[:n])
+    return out
+
+
+def decode_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE,
+                 freeze: int = FREEZE_OFF, fp32: bool = False, nthreads: int = 0):
+    """Decode a [batch, N] LLR array; returns (u_hat, iters, pe, margin)."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    B, N = llr.shape
+    u_hat = np.zeros((B, N), np.uint8)
+    iters = np.zeros(B, np.int32)
+    pe = np.zeros(B, np.int64)
+    margin = np.zeros(B, np.float64)
+    rc = _load().orc_decode_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B, max_iter, alpha,
+                                  stop, freeze, 1 if fp32 else 0, nthreads, _p(u_hat, ctypes.c_uint8),
+                                  _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double))
+    _check(rc, "decode_batch")
+    return u_hat, iters, pe, margin

@@ -1,0 +1,515 @@
+/*
+ * polar_oracle.c -- plain, slow CPU oracle for belief-propagation (BP)
+ * decoding of polar codes with the G-matrix early stop and the paper's
+ * connected-sub-factor-graph (CSFG) freezing.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  The GPU library shares no
+ * code, header, table or helper with it.
+ *
+ * Paper: S. M. Abbas, Y. Fan, J. Chen, C.-Y. Tsui, "Low Complexity Belief
+ * Propagation Polar Code Decoder", arXiv 1505.04979.
+ *
+ *   code, frozen set, x = u F^{(x)m} .......... Sec. II
+ *   factor graph, min-sum PE update ............ Sec. II-A, Eq. (1)
+ *   CSFG, freezing order ....................... Sec. III
+ *   hard decision / inverse / frozen test ...... Sec. III, Eqs. (2)-(4), Lemma 1
+ *   +-infinity feedback of a frozen CSFG ....... Sec. III (equation after Lemma 1)
+ *   computation count .......................... Sec. IV
+ *
+ * Index conventions (0-based).  Node columns c = 0..m; column 0 is the channel
+ * side (the paper's stage 1) and column m the source side (the paper's stage
+ * m+1).  PE stage s = 0..m-1 joins columns s and s+1 (the paper's stage
+ * j = s+1) and pairs node a with node b = a + 2^(m-1-s).  Level j = 1..m holds
+ * the 2^j CSFGs of the paper's stage j, each of size 2^(m-j); CSFG k of level
+ * j covers source indices [k 2^(m-j), (k+1) 2^(m-j)) and is fed by R[j].
+ *
+ * Readings of the paper that this file fixes (every one is also listed in the
+ * design notes):
+ *   R1  one left-to-right sweep per iteration; R from this iteration, L from
+ *       the previous one, exactly as Eq. (1) is written (Sec. II-A).
+ *   R2  interior L messages start at 0; L[m] is the prior: +inf on frozen
+ *       positions, 0 on information positions.
+ *   R3  level j is checked right after PE stage j-1 (it consumes R[j]), and
+ *       only its first CSFG that is not yet covered is checked, once per
+ *       iteration (Sec. III; Fig. 5 captions).
+ *   R4  a CSFG is "covered" when it, or a CSFG containing it, is frozen.  A
+ *       CSFG whose two halves are both covered is frozen at that moment, with
+ *       the hard decision obtained by re-encoding the stored source bits of
+ *       its range (the +-inf messages its own PEs would emit).
+ *   R5  the PEs of stage s >= 1 inside a covered level-s CSFG are skipped and
+ *       not counted; stage 0 always runs.
+ *   R6  Eq. (2) maps values >= 0 (including -0) to 0.
+ *   R7  G-matrix stop: u_hat (stored bits on covered indices, HD(R[m]+L[m])
+ *       elsewhere, 0 on frozen indices) re-encoded must equal HD(R[0]+L[0]).
+ *   R8  freeze-only decoding ends when every index is covered; the output is
+ *       the stored bits on covered indices and HD(R[m]+L[m]) elsewhere.
+ *
+ * Precision.  By default every message is an IEEE double.  With fp32 != 0
+ * every arithmetic result is rounded to binary32 right after it is formed,
+ * which reproduces single-precision arithmetic operation by operation (sums of
+ * two binary32 values are exact or correctly rounded once in binary64, and
+ * rounding binary64 to binary32 after a single add or multiply is innocuous);
+ * this lets hard decisions be compared in the precision a GPU kernel uses.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_NOMEM (-2)
+#define ORC_ERR_PREFIX (-3)
+#define ORC_ERR_NAN (-4)
+
+static int ilog2_exact(int n)
+{
+    int m = 0;
+    if (n < 1) return -1;
+    while ((1 << m) < n) ++m;
+    return ((1 << m) == n) ? m : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. II: frozen set.  The paper does not say how the reliable positions   */
+/* are found; the Bhattacharyya recursion of a binary erasure channel with    */
+/* erasure probability z0 is used.  A channel with parameter z splits into    */
+/* a worse one, 2z - z^2, and a better one, z^2; after m splits, position i   */
+/* carries the channel whose split decisions are the bits of i read from the  */
+/* most significant bit (first split) to the least significant (last split),  */
+/* 0 = worse, 1 = better.  The recursion runs on (ln z, ln(1 - z)) so that    */
+/* neither tail rounds to 0 or 1:                                             */
+/*   worse:  ln z' = ln z + log1p(1 - z),   ln(1 - z') = 2 ln(1 - z)           */
+/*   better: ln z' = 2 ln z,                ln(1 - z') = ln(1 - z) + log1p(z)  */
+/* ------------------------------------------------------------------------ */
+int orc_bec_lnz(int N, double z0, double* ln_z, double* ln_1mz)
+{
+    int m = ilog2_exact(N);
+    if (m < 0 || !(z0 > 0.0 && z0 < 1.0) || !ln_z || !ln_1mz) return ORC_ERR_ARG;
+    ln_z[0] = log(z0);
+    ln_1mz[0] = log1p(-z0);
+    for (int level = 0; level < m; ++level) {
+        int count = 1 << level;
+        /* walk backwards so that entry k is read before 2k and 2k+1 are written */
+        for (int k = count - 1; k >= 0; --k) {
+            double a = ln_z[k], b = ln_1mz[k];
+            double worse_a = a + log1p(exp(b));
+            double worse_b = 2.0 * b;
+            double better_a = 2.0 * a;
+            double better_b = b + log1p(exp(a));
+            ln_z[2 * k] = worse_a;
+            ln_1mz[2 * k] = worse_b;
+            ln_z[2 * k + 1] = better_a;
+            ln_1mz[2 * k + 1] = better_b;
+        }
+    }
+    return ORC_OK;
+}
+
+typedef struct {
+    double logit;
+    int index;
+} rank_t;
+
+static int rank_cmp(const void* pa, const void* pb)
+{
+    const rank_t* a = (const rank_t*)pa;
+    const rank_t* b = (const rank_t*)pb;
+    if (a->logit < b->logit) return -1;
+    if (a->logit > b->logit) return 1;
+    /* equal reliability: the larger index counts as the more reliable one */
+    return (a->index > b->index) ? -1 : (a->index < b->index);
+}
+
+/* frozen[i] = 1 for the N-K least reliable positions (largest z). */
+int orc_bec_frozen(int N, int K, double z0, uint8_t* frozen)
+{
+    int m = ilog2_exact(N);
+    if (m < 0 || K < 0 || K > N || !frozen) return ORC_ERR_ARG;
+    double* a = (double*)malloc(sizeof(double) * (size_t)N);
+    double* b = (double*)malloc(sizeof(double) * (size_t)N);
+    rank_t* r = (rank_t*)malloc(sizeof(rank_t) * (size_t)N);
+    if (!a || !b || !r) {
+        free(a);
+        free(b);
+        free(r);
+        return ORC_ERR_NOMEM;
+    }
+    int rc = orc_bec_lnz(N, z0, a, b);
+    if (rc == ORC_OK) {
+        for (int i = 0; i < N; ++i) {
+            r[i].logit = a[i] - b[i]; /* ln(z / (1 - z)), increasing in z */
+            r[i].index = i;
+        }
+        qsort(r, (size_t)N, sizeof(rank_t), rank_cmp);
+        for (int i = 0; i < N; ++i) frozen[i] = 1;
+        for (int i = 0; i < K; ++i) frozen[r[i].index] = 0;
+    }
+    free(a);
+    free(b);
+    free(r);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. II, Eq. (3): out = in . F^{(x)k} over GF(2), n = 2^k.                 */
+/* F^{(x)k} = [[F^{(x)k-1}, 0], [F^{(x)k-1}, F^{(x)k-1}]], so a row vector     */
+/* [p, q] maps to [(p xor q) F^{(x)k-1}, q F^{(x)k-1}].  scratch needs n bytes.*/
+/* ------------------------------------------------------------------------ */
+static void polar_transform(const uint8_t* in, uint8_t* out, int n, uint8_t* scratch)
+{
+    if (n == 1) {
+        out[0] = in[0];
+        return;
+    }
+    int h = n / 2;
+    uint8_t* tmp = scratch;
+    for (int i = 0; i < h; ++i) tmp[i] = (uint8_t)(in[i] ^ in[i + h]);
+    polar_transform(tmp, out, h, scratch + h);
+    polar_transform(in + h, out + h, h, scratch + h);
+}
+
+int orc_encode(int N, const uint8_t* u, uint8_t* x)
+{
+    if (ilog2_exact(N) < 0 || !u || !x) return ORC_ERR_ARG;
+    uint8_t* scratch = (uint8_t*)malloc((size_t)N);
+    uint8_t* in = (uint8_t*)malloc((size_t)N);
+    if (!scratch || !in) {
+        free(scratch);
+        free(in);
+        return ORC_ERR_NOMEM;
+    }
+    for (int i = 0; i < N; ++i) in[i] = (uint8_t)(u[i] & 1);
+    polar_transform(in, x, N, scratch);
+    free(scratch);
+    free(in);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eqs. (2)-(4) on one CSFG of size S with inputs Rin (Lemma 1: when this     */
+/* returns 1, uh is the maximum-likelihood source word of the constituent     */
+/* code).  xh, uh get S bytes; scratch needs S bytes.                         */
+/* ------------------------------------------------------------------------ */
+int orc_csfg_check(int S, const double* Rin, const uint8_t* frozen_sub, uint8_t* xh, uint8_t* uh,
+                   uint8_t* scratch)
+{
+    for (int i = 0; i < S; ++i) xh[i] = (Rin[i] < 0.0) ? 1 : 0; /* Eq. (2) */
+    polar_transform(xh, uh, S, scratch);                           /* Eq. (3) */
+    for (int i = 0; i < S; ++i)
+        if (frozen_sub[i] && uh[i]) return 0; /* Eq. (4) fails */
+    return 1;
+}
+
+/* public wrapper with its own scratch, for the brute-force Lemma 1 test */
+int orc_csfg_check_ext(int S, const double* Rin, const uint8_t* frozen_sub, uint8_t* xh, uint8_t* uh)
+{
+    if (ilog2_exact(S) < 0) return ORC_ERR_ARG;
+    uint8_t* scratch = (uint8_t*)malloc((size_t)S);
+    if (!scratch) return ORC_ERR_NOMEM;
+    int r = orc_csfg_check(S, Rin, frozen_sub, xh, uh, scratch);
+    free(scratch);
+    return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Decoder                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int N, m;
+    int fp32;
+    double alpha;
+    const uint8_t* frozen;
+    double* L;          /* (m+1) x N */
+    double* R;          /* (m+1) x N */
+    uint8_t* blk;       /* per-level frozen flags: level j block k at blk[(1<<j) + k] */
+    uint8_t* ustore;    /* decided source bits of covered indices */
+    uint8_t* xh;        /* N */
+    uint8_t* uh;        /* N */
+    uint8_t* scratch;   /* N */
+    uint8_t* ubits;     /* N */
+    uint8_t* xbits;     /* N */
+    int64_t pe;
+    double margin;
+    int nan_seen;
+} dec_t;
+
+#define LM(d, c, i) ((d)->L[(size_t)(c) * (size_t)(d)->N + (size_t)(i)])
+#define RM(d, c, i) ((d)->R[(size_t)(c) * (size_t)(d)->N + (size_t)(i)])
+
+static double rnd(const dec_t* d, double v) { return d->fp32 ? (double)(float)v : v; }
+
+static double sgn(double v) { return (double)((v > 0.0) - (v < 0.0)); }
+
+/* scaled min-sum: alpha sign(x) sign(y) min(|x|, |y|)   (Eq. (1)) */
+static double fms(const dec_t* d, double x, double y)
+{
+    return rnd(d, d->alpha * sgn(x) * sgn(y) * fmin(fabs(x), fabs(y)));
+}
+
+static void note_margin(dec_t* d, double v)
+{
+    double a = fabs(v);
+    if (a < d->margin) d->margin = a;
+}
+
+/* A CSFG is covered when it or one of the CSFGs that contain it is frozen. */
+static int covered(const dec_t* d, int j, int k)
+{
+    for (int jj = j; jj >= 1; --jj) {
+        if (d->blk[(1 << jj) + (k >> (j - jj))]) return 1;
+    }
+    return 0;
+}
+
+static int index_covered(const dec_t* d, int i) { return covered(d, d->m, i); }
+
+/* Length of the covered prefix; returns -1 when the covered set is not a prefix. */
+static int covered_prefix(const dec_t* d)
+{
+    int P = 0;
+    while (P < d->N && index_covered(d, P)) ++P;
+    for (int i = P; i < d->N; ++i)
+        if (index_covered(d, i)) return -1;
+    return P;
+}
+
+/* Fix the feedback of a frozen CSFG: L[j][block] = (-1)^xh * inf. */
+static void set_feedback(dec_t* d, int j, int base, int S, const uint8_t* xh)
+{
+    for (int i = 0; i < S; ++i) LM(d, j, base + i) = xh[i] ? -INFINITY : INFINITY;
+}
+
+/* Freeze CSFG (j, k) with hard decision xh and source word uh, then freeze every
+ * enclosing CSFG whose two halves have become covered (reading R4). */
+static void freeze_block(dec_t* d, int j, int k, const uint8_t* xh, const uint8_t* uh)
+{
+    int S = d->N >> j;
+    int base = k * S;
+    d->blk[(1 << j) + k] = 1;
+    memcpy(d->ustore + base, uh, (size_t)S);
+    set_feedback(d, j, base, S, xh);
+    while (j > 1) {
+        int sib = k ^ 1;
+        if (!covered(d, j, sib)) break;
+        j -= 1;
+        k >>= 1;
+        S = d->N >> j;
+        base = k * S;
+        d->blk[(1 << j) + k] = 1;
+        /* the hard decision of the parent is its stored source bits re-encoded */
+        polar_transform(d->ustore + base, d->xbits, S, d->scratch);
+        set_feedback(d, j, base, S, d->xbits);
+    }
+}
+
+/* Check the first uncovered CSFG of level j (reading R3). */
+static void check_level(dec_t* d, int j)
+{
+    int S = d->N >> j;
+    int nblk = 1 << j;
+    int k = 0;
+    while (k < nblk && covered(d, j, k)) ++k;
+    if (k == nblk) return;
+    int base = k * S;
+    const double* Rin = &RM(d, j, base);
+    for (int i = 0; i < S; ++i) note_margin(d, Rin[i]);
+    if (orc_csfg_check(S, Rin, d->frozen + base, d->xh, d->uh, d->scratch))
+        freeze_block(d, j, k, d->xh, d->uh);
+}
+
+/* PE stage s (Eq. (1)), skipping PEs inside covered CSFGs (reading R5). */
+static void pe_stage(dec_t* d, int s)
+{
+    const int N = d->N, m = d->m;
+    const int h = 1 << (m - 1 - s);
+    for (int a = 0; a < N; ++a) {
+        if (a & h) continue;
+        if (s >= 1 && covered(d, s, a >> (m - s))) continue;
+        const int b = a + h;
+        const double La = LM(d, s + 1, a); /* L^{t-1}_{i,j+1}       */
+        const double Lb = LM(d, s + 1, b); /* L^{t-1}_{i+2^(m-j),j+1} */
+        const double Ra = RM(d, s, a);     /* R^t_{i,j}             */
+        const double Rb = RM(d, s, b);     /* R^t_{i+2^(m-j),j}     */
+        const double t = rnd(d, Lb + Rb);
+        const double g = fms(d, La, Ra);
+        const double nLa = fms(d, La, t);
+        const double nLb = rnd(d, Lb + g);
+        const double nRa = fms(d, Ra, t);
+        const double nRb = rnd(d, Rb + g);
+        if (isnan(nLa) || isnan(nLb) || isnan(nRa) || isnan(nRb)) d->nan_seen = 1;
+        LM(d, s, a) = nLa;
+        LM(d, s, b) = nLb;
+        RM(d, s + 1, a) = nRa;
+        RM(d, s + 1, b) = nRb;
+        d->pe += 1;
+    }
+}
+
+/* source-side decision for index i (readings R7, R8) */
+static uint8_t source_bit(dec_t* d, int i, int use_store)
+{
+    if (use_store && index_covered(d, i)) return d->ustore[i];
+    if (d->frozen[i]) return 0;
+    double v = rnd(d, RM(d, d->m, i) + LM(d, d->m, i));
+    note_margin(d, v);
+    return (v < 0.0) ? 1 : 0;
+}
+
+/* G-matrix stop (reading R7): u_hat . G == HD(R[0] + L[0]) */
+static int gmatrix_stop(dec_t* d, int use_store)
+{
+    const int N = d->N;
+    for (int i = 0; i < N; ++i) d->ubits[i] = source_bit(d, i, use_store);
+    polar_transform(d->ubits, d->uh, N, d->scratch);
+    int same = 1;
+    for (int i = 0; i < N; ++i) {
+        double v = rnd(d, RM(d, 0, i) + LM(d, 0, i));
+        note_margin(d, v);
+        uint8_t x = (v < 0.0) ? 1 : 0;
+        if (x != d->uh[i]) same = 0;
+    }
+    return same;
+}
+
+/*
+ * Decode one codeword.
+ *   llr        N channel LLRs, log P(x=0)/P(x=1), as binary32
+ *   stop_mode  0 = fixed iterations, 1 = G-matrix stop
+ *   freeze     0 = off, 1 = CSFG freezing
+ *   u_hat      N output bytes (0/1)
+ *   iters      iterations executed; pe = PE updates executed (Sec. IV count)
+ *   margin     smallest |value| a hard decision was taken on (may be NULL)
+ *   trace_L, trace_R   optional max_iter x (m+1) x N planes after each iteration
+ *   trace_P    optional max_iter entries: covered-prefix length after each iteration
+ *   trace_pe   optional max_iter entries: PE updates in each iteration
+ * Returns ORC_OK, or a negative error code.
+ */
+int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, double alpha, int stop_mode,
+               int freeze, int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin,
+               double* trace_L, double* trace_R, int32_t* trace_P, int64_t* trace_pe)
+{
+    int m = ilog2_exact(N);
+    if (m < 1 || !frozen || !llr || max_iter < 1 || !(alpha > 0.0) || !u_hat) return ORC_ERR_ARG;
+    dec_t d;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.m = m;
+    d.fp32 = fp32;
+    d.alpha = fp32 ? (double)(float)alpha : alpha;
+    d.frozen = frozen;
+    d.margin = INFINITY;
+    size_t planes = (size_t)(m + 1) * (size_t)N;
+    d.L = (double*)calloc(planes, sizeof(double));
+    d.R = (double*)calloc(planes, sizeof(double));
+    d.blk = (uint8_t*)calloc((size_t)2 * (size_t)N, 1);
+    d.ustore = (uint8_t*)calloc((size_t)N, 1);
+    d.xh = (uint8_t*)malloc((size_t)N);
+    d.uh = (uint8_t*)malloc((size_t)N);
+    d.scratch = (uint8_t*)malloc((size_t)N);
+    d.ubits = (uint8_t*)malloc((size_t)N);
+    d.xbits = (uint8_t*)malloc((size_t)N);
+    int rc = ORC_OK;
+    if (!d.L || !d.R || !d.blk || !d.ustore || !d.xh || !d.uh || !d.scratch || !d.ubits || !d.xbits) {
+        rc = ORC_ERR_NOMEM;
+        goto out;
+    }
+    /* reading R2: prior on the source side, zero elsewhere */
+    for (int i = 0; i < N; ++i) LM(&d, m, i) = frozen[i] ? INFINITY : 0.0;
+
+    int done = 0, t_done = max_iter;
+    for (int t = 1; t <= max_iter && !done; ++t) {
+        int64_t pe_before = d.pe;
+        for (int i = 0; i < N; ++i) RM(&d, 0, i) = (double)llr[i];
+        for (int s = 0; s < m; ++s) {
+            if (freeze && s >= 1) {
+                check_level(&d, s);
+                if (covered_prefix(&d) == N) {
+                    done = 1;
+                    break;
+                }
+            }
+            pe_stage(&d, s);
+        }
+        if (!done && freeze) {
+            check_level(&d, m);
+            if (covered_prefix(&d) == N) done = 1;
+        }
+        if (!done && stop_mode == 1) {
+            if (gmatrix_stop(&d, freeze)) done = 1;
+        }
+        int P = covered_prefix(&d);
+        if (P < 0) {
+            rc = ORC_ERR_PREFIX;
+            goto out;
+        }
+        if (d.nan_seen) {
+            rc = ORC_ERR_NAN;
+            goto out;
+        }
+        if (trace_L) memcpy(trace_L + (size_t)(t - 1) * planes, d.L, planes * sizeof(double));
+        if (trace_R) memcpy(trace_R + (size_t)(t - 1) * planes, d.R, planes * sizeof(double));
+        if (trace_P) trace_P[t - 1] = P;
+        if (trace_pe) trace_pe[t - 1] = d.pe - pe_before;
+        if (done) t_done = t;
+    }
+    for (int i = 0; i < N; ++i) u_hat[i] = source_bit(&d, i, freeze);
+    if (iters) *iters = t_done;
+    if (pe) *pe = d.pe;
+    if (margin) *margin = d.margin;
+out:
+    free(d.L);
+    free(d.R);
+    free(d.blk);
+    free(d.ustore);
+    free(d.xh);
+    free(d.uh);
+    free(d.scratch);
+    free(d.ubits);
+    free(d.xbits);
+    return rc;
+}
+
+/* Decode `batch` codewords (llr is batch x N), threaded over codewords when the
+ * file is built with OpenMP.  nthreads <= 0 uses the OpenMP default.  Returns
+ * the first nonzero error code met, else ORC_OK. */
+int orc_decode_batch(int N, const uint8_t* frozen, const float* llr, int batch, int max_iter, double alpha,
+                     int stop_mode, int freeze, int fp32, int nthreads, uint8_t* u_hat, int32_t* iters,
+                     int64_t* pe, double* margin)
+{
+    if (batch < 0) return ORC_ERR_ARG;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+#endif
+    for (int c = 0; c < batch; ++c) {
+        int r = orc_decode(N, frozen, llr + (size_t)c * (size_t)N, max_iter, alpha, stop_mode, freeze, fp32,
+                           u_hat + (size_t)c * (size_t)N, iters ? iters + c : NULL, pe ? pe + c : NULL,
+                           margin ? margin + c : NULL, NULL, NULL, NULL, NULL);
+        if (r != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            {
+                if (err == ORC_OK) err = r;
+            }
+        }
+    }
+    (void)nthreads;
+    return err;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

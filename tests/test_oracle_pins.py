@@ -1,0 +1,339 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names the passage of arXiv 1505.04979 it pins and what fixes the
+expected value: a brute-force enumeration, a library routine standing in for a
+textbook definition (np.kron), a hand-derived closed form (tests/golden), an
+invariant derived by hand, or maximum-likelihood decoding by exhaustive search.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04979_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+F = np.array([[1, 0], [1, 1]], dtype=np.int64)
+
+
+def kron_G(N):
+    """G = F^{(x)m} built with numpy's Kronecker product (Sec. II)."""
+    G = np.ones((1, 1), np.int64)
+    while G.shape[0] < N:
+        G = np.kron(G, F)
+    return G
+
+
+# --------------------------------------------------------------------------
+# Sec. II: frozen set from the BEC recursion, pinned by brute-force erasure
+# enumeration of the synthetic channels under successive cancellation.
+# --------------------------------------------------------------------------
+def _in_span(target, vectors):
+    """GF(2) membership of bitmask `target` in the span of bitmask `vectors`."""
+    basis = {}
+    for v in vectors:
+        while v:
+            h = v.bit_length() - 1
+            if h in basis:
+                v ^= basis[h]
+            else:
+                basis[h] = v
+                break
+    t = target
+    while t:
+        h = t.bit_length() - 1
+        if h not in basis:
+            return False
+        t ^= basis[h]
+    return True
+
+
+def brute_force_erasure(N, z0):
+    """Erasure probability of u_i given u_0..u_{i-1} when every x_c is erased with prob z0."""
+    G = kron_G(N)
+    z = np.zeros(N)
+    for pattern in range(1 << N):
+        erased = [(pattern >> c) & 1 for c in range(N)]
+        ne = sum(erased)
+        p = (z0 ** ne) * ((1 - z0) ** (N - ne))
+        for i in range(N):
+            # unknowns u_i..u_{N-1}; bit r-i of a mask stands for u_r
+            cols = []
+            for c in range(N):
+                if not erased[c]:
+                    mask = 0
+                    for r in range(i, N):
+                        if G[r, c]:
+                            mask |= 1 << (r - i)
+                    cols.append(mask)
+            if not _in_span(1, cols):
+                z[i] += p
+    return z
+
+
+@pytest.mark.parametrize("N", [2, 4, 8])
+@pytest.mark.parametrize("z0", [0.5, 0.3])
+def test_bec_z_matches_brute_force_erasure(N, z0):
+    a, _ = O.bec_lnz(N, z0)
+    np.testing.assert_allclose(np.exp(a), brute_force_erasure(N, z0), rtol=0, atol=1e-12)
+
+
+def test_bec_8_4_frozen_set():
+    """The (8,4) code of Sec. III (Figs. 3-5): frozen set {0,1,2,4}, from the brute-force z."""
+    z = brute_force_erasure(8, 0.5)
+    expected = set(np.argsort(-z, kind="stable")[:4].tolist())
+    assert expected == {0, 1, 2, 4}
+    assert set(np.nonzero(O.bec_frozen(8, 4))[0].tolist()) == {0, 1, 2, 4}
+
+
+CODE_SIZES = [(16, 8), (64, 32), (128, 64), (256, 64), (256, 128), (256, 192), (1024, 256), (1024, 512),
+              (1024, 768), (4096, 1024), (4096, 2048), (4096, 3072), (8192, 4096), (16384, 8192),
+              (32768, 16384)]
+
+
+@pytest.mark.parametrize("N,K", CODE_SIZES)
+def test_frozen_set_size_and_partial_order(N, K):
+    """|A^c| = N-K, and the information set is closed upward in the bitwise partial
+    order of polar channels (if i is information and j covers i bitwise, j is information)."""
+    fz = O.bec_frozen(N, K)
+    assert int(fz.sum()) == N - K
+    info = fz == 0
+    for b in range(N.bit_length() - 1):
+        i = np.arange(N)
+        has = (i >> b) & 1
+        lo = i[has == 0]
+        hi = lo | (1 << b)
+        assert not np.any(info[lo] & ~info[hi])
+
+
+@pytest.mark.parametrize("N", [64, 1024, 32768])
+def test_bec_sum_is_conserved(N):
+    """A BEC split preserves the sum of erasure probabilities: sum z = N z0."""
+    a, _ = O.bec_lnz(N, 0.5)
+    assert math.isclose(float(np.exp(a).sum()), N * 0.5, rel_tol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Sec. II: encoder x = u F^{(x)m}
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
+def test_encoder_matches_dense_kronecker(N):
+    G = kron_G(N)
+    for u in itertools.product([0, 1], repeat=N) if N <= 8 else np.random.default_rng(0).integers(0, 2, (300, N)):
+        u = np.array(u, np.uint8)
+        assert np.array_equal(O.encode(u), (u.astype(np.int64) @ G % 2).astype(np.uint8))
+
+
+@pytest.mark.parametrize("N", [2, 64, 1024])
+def test_encoder_is_an_involution(N):
+    """Eq. (3): (F^{(x)m})^{-1} = F^{(x)m}."""
+    u = np.random.default_rng(N).integers(0, 2, (20, N)).astype(np.uint8)
+    assert np.array_equal(O.encode(O.encode(u)), u)
+
+
+# --------------------------------------------------------------------------
+# Eq. (2)-(4) and Lemma 1: brute-force maximum likelihood on constituent codes
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("S", [2, 4, 8, 16])
+def test_lemma1_check_implies_ml(S):
+    rng = np.random.default_rng(S)
+    G = kron_G(S)
+    passes = 0
+    for trial in range(300):
+        nfz = rng.integers(1 if S > 2 else 0, S)
+        fz = np.zeros(S, np.uint8)
+        fz[rng.choice(S, nfz, replace=False)] = 1
+        if (fz == 0).sum() > 10:
+            continue
+        # LLRs of a valid codeword plus noise, so the check passes often enough
+        u = rng.integers(0, 2, S) * (1 - fz)
+        x = u @ G % 2
+        R = (1 - 2 * x) * 2.0 + rng.normal(0, 1.0 + trial % 3, S)
+        ok, xh, uh = O.csfg_check(R, fz)
+        # the check's hard decisions are Eq. (2) and its source word is Eq. (3)
+        assert np.array_equal(xh, (R < 0).astype(np.uint8))
+        if not ok:
+            assert np.any(uh[fz == 1] == 1)
+            continue
+        passes += 1
+        info = np.nonzero(fz == 0)[0]
+        U = np.zeros((1 << len(info), S), np.int64)
+        U[:, info] = np.array(list(itertools.product([0, 1], repeat=len(info))), np.int64).reshape(-1, len(info))
+        best = float(np.max((1 - 2 * (U @ G % 2)) @ R))
+        xu = uh.astype(np.int64) @ G % 2
+        like = float(np.sum((1 - 2 * xu) * R))
+        assert abs(like - best) < 1e-9
+        assert abs(like - np.abs(R).sum()) < 1e-9  # the bound used in the proof of Lemma 1
+    assert passes > 20
+
+
+def test_eq2_maps_zero_to_zero():
+    """Eq. (2): values >= 0, including -0.0, decide 0."""
+    ok, xh, uh = O.csfg_check(np.array([0.0, -0.0, -1.0, 2.0]), np.zeros(4, np.uint8))
+    assert xh.tolist() == [0, 0, 1, 0]
+
+
+# --------------------------------------------------------------------------
+# Eq. (1): closed forms worked by hand
+# --------------------------------------------------------------------------
+def test_n2_is_the_repetition_ml_decoder():
+    """(2,1) code, frozen {0}: with alpha = 1 BP decides u_1 = [y_0 + y_1 < 0],
+    the maximum-likelihood decision of a length-2 repetition code."""
+    rng = np.random.default_rng(2)
+    fz = np.array([1, 0], np.uint8)
+    for _ in range(500):
+        y = rng.normal(0, 3, 2).astype(np.float32)
+        if abs(float(y[0]) + float(y[1])) < 1e-6:
+            continue
+        for it in (1, 4):
+            r = O.decode(fz, y, it, alpha=1.0)
+            assert r["u_hat"].tolist() == [0, int(float(y[0]) + float(y[1]) < 0)]
+
+
+def test_n2_first_iteration_messages():
+    """(2,1) code, frozen {0}, L[1] = [inf, 0]: after iteration 1, R[1] = [f(y0, y1), y1 + alpha y0]
+    and L[0] = [f(inf, y1), 0 + f(inf, y0)] = [alpha y1, alpha y0] (Eq. (1) by hand)."""
+    y = np.array([1.5, -0.25], np.float32)
+    r = O.decode(np.array([1, 0], np.uint8), y, 1, alpha=0.5, trace=True)
+    R1 = r["R"][0][1]
+    L0 = r["L"][0][0]
+    assert R1.tolist() == [-0.125, -0.25 + 0.75]  # f(y0, y1): alpha*sgn*sgn*min = -0.125
+    assert L0.tolist() == [0.5 * -0.25, 0.5 * 1.5]  # f(inf, y1) = alpha y1; 0 + f(inf, y0)
+
+
+def test_n4_closed_form_two_iterations():
+    g = json.load(open(os.path.join(GOLDEN, "n4_closed_form.json")))
+    conv = lambda v: [np.inf if e == "inf" else (-np.inf if e == "-inf" else e) for e in v]
+    r = O.decode(np.array(g["frozen"], np.uint8), np.array(g["llr"], np.float32), 2, alpha=g["alpha"], trace=True)
+    for it, key in ((0, "iter1"), (1, "iter2")):
+        e = g[key]
+        assert r["R"][it][1].tolist() == conv(e["R1"])
+        assert r["R"][it][2].tolist() == conv(e["R2"])
+        assert r["L"][it][0].tolist() == conv(e["L0"])
+        assert r["L"][it][1].tolist() == conv(e["L1"])
+    assert r["u_hat"].tolist() == g["u_hat"]
+
+
+def test_n4_is_two_repetition_codes():
+    """(4,2) code, frozen {0,1}: x = (u2^u3, u3, u2^u3, u3), two repetition codes.
+    With alpha = 1, BP (two or more iterations) gives their ML decisions."""
+    rng = np.random.default_rng(4)
+    fz = np.array([1, 1, 0, 0], np.uint8)
+    for _ in range(400):
+        y = rng.normal(0, 2, 4).astype(np.float32)
+        s02 = float(y[0]) + float(y[2])
+        s13 = float(y[1]) + float(y[3])
+        if min(abs(s02), abs(s13)) < 1e-6:
+            continue
+        u3 = int(s13 < 0)
+        u2 = int(s02 < 0) ^ u3
+        for it in (2, 7):
+            assert O.decode(fz, y, it, alpha=1.0)["u_hat"].tolist() == [0, 0, u2, u3]
+
+
+# --------------------------------------------------------------------------
+# Noiseless input: invariants derived by hand (iteration 1 of the sweep yields
+# the correct hard decisions at every level, so every check passes)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [8, 64, 1024])
+@pytest.mark.parametrize("frac", [0.25, 0.5, 0.75])
+def test_noiseless_invariants(N, frac):
+    K = int(N * frac)
+    m = N.bit_length() - 1
+    fz = O.bec_frozen(N, K)
+    u = I.info_bits(11, np.arange(4), fz)
+    x = O.encode(u)
+    llr = I.noiseless_llr(x, 2.5)
+    for c in range(4):
+        r = O.decode(fz, llr[c], 30, stop=O.STOP_GMATRIX)
+        assert (r["iters"], r["pe"]) == (1, m * N // 2) and np.array_equal(r["u_hat"], u[c])
+        r = O.decode(fz, llr[c], 30, freeze=O.FREEZE_CSFG)
+        assert (r["iters"], r["pe"]) == (2, 3 * N // 2 - 1) and np.array_equal(r["u_hat"], u[c])
+        r = O.decode(fz, llr[c], 30, stop=O.STOP_GMATRIX, freeze=O.FREEZE_CSFG)
+        assert (r["iters"], r["pe"]) == (1, N - 1) and np.array_equal(r["u_hat"], u[c])
+        for it in (1, 5):
+            r = O.decode(fz, llr[c], it)
+            assert (r["iters"], r["pe"]) == (it, it * m * N // 2) and np.array_equal(r["u_hat"], u[c])
+
+
+# --------------------------------------------------------------------------
+# Invariants on noisy decodes
+# --------------------------------------------------------------------------
+def _noisy(N, K, B, ebn0, seed):
+    fz = O.bec_frozen(N, K)
+    idx = np.arange(B)
+    u = I.info_bits(seed, idx, fz)
+    x = O.encode(u)
+    llr = I.channel_llr(x, I.gaussian(seed, idx, N), I.sigma(ebn0, K / N))
+    return fz, u, x, llr
+
+
+@pytest.mark.parametrize("N", [16, 64, 256])
+def test_freezing_invariants_on_noisy_input(N):
+    """Sec. III: R messages stay finite; the covered set only grows; frozen outputs
+    are 0; and every +-inf feedback plane agrees with one PE butterfly of the
+    plane to its right (what Eq. (1) yields on +-inf inputs), which is reading R4."""
+    m = N.bit_length() - 1
+    fz, u, x, llr = _noisy(N, N // 2, 40, 2.0, 5)
+    saw_inf_pair = 0
+    for c in range(llr.shape[0]):
+        for stop in (O.STOP_NONE, O.STOP_GMATRIX):
+            r = O.decode(fz, llr[c], 25, stop=stop, freeze=O.FREEZE_CSFG, trace=True)
+            assert np.all(np.isfinite(r["R"]))
+            assert np.all(np.diff(r["P"]) >= 0)
+            assert np.all(r["u_hat"][fz == 1] == 0)
+            assert int(r["pe_iter"].sum()) == r["pe"]
+            L = r["L"][-1]
+            for j in range(1, m):
+                S = N >> j
+                for k in range(1 << j):
+                    blk = slice(k * S, (k + 1) * S)
+                    if np.all(np.isinf(L[j, blk])) and np.all(np.isinf(L[j + 1, blk])):
+                        h = S // 2
+                        xa = L[j + 1, k * S:k * S + h] < 0
+                        xb = L[j + 1, k * S + h:(k + 1) * S] < 0
+                        got = L[j, blk] < 0
+                        assert np.array_equal(got[:h], xa ^ xb) and np.array_equal(got[h:], xb)
+                        saw_inf_pair += 1
+    assert saw_inf_pair > 0
+
+
+def test_fp32_mode_rounds_every_message():
+    fz, u, x, llr = _noisy(64, 32, 8, 2.5, 9)
+    for c in range(8):
+        r = O.decode(fz, llr[c], 12, stop=O.STOP_GMATRIX, freeze=O.FREEZE_CSFG, fp32=True, trace=True)
+        for planes in (r["L"], r["R"]):
+            finite = planes[np.isfinite(planes)]
+            assert np.array_equal(finite, finite.astype(np.float32).astype(np.float64))
+
+
+def test_fp32_and_fp64_agree_away_from_thresholds():
+    fz, u, x, llr = _noisy(256, 128, 60, 2.5, 3)
+    a = O.decode_batch(fz, llr, 40, stop=O.STOP_GMATRIX, freeze=O.FREEZE_CSFG)
+    b = O.decode_batch(fz, llr, 40, stop=O.STOP_GMATRIX, freeze=O.FREEZE_CSFG, fp32=True)
+    # a decision taken on a value this far from 0 cannot flip under binary32 rounding here
+    safe = a[3] > 1e-4
+    assert safe.sum() > 40
+    assert np.array_equal(a[0][safe], b[0][safe])
+    assert np.array_equal(a[1][safe], b[1][safe])
+
+
+def test_statistics_at_3db_are_plausible():
+    """Sec. IV, (1024,512), alpha = 0.9375, max_iter = 40, 3 dB: the paper reports no FER
+    loss from either stop rule and about 26 G-matrix iterations (derived from its -46%/-17%
+    figures).  These pin only loosely: 300 codewords."""
+    fz, u, x, llr = _noisy(1024, 512, 300, 3.0, 21)
+    res = {}
+    for mode in ((0, 0), (1, 0), (1, 1), (0, 1)):
+        uh, it, pe, _ = O.decode_batch(fz, llr, 40, stop=mode[0], freeze=mode[1])
+        res[mode] = ((uh != u).any(1).mean(), it.mean(), pe.mean())
+    assert res[(0, 0)][0] < 0.08
+    for mode in res:
+        assert abs(res[mode][0] - res[(0, 0)][0]) <= 0.02
+    assert 18.0 < res[(1, 0)][1] < 32.0
+    assert res[(1, 1)][2] <= res[(1, 0)][2]
+    assert res[(0, 1)][2] < res[(0, 0)][2]
