@@ -1,0 +1,391 @@
+"""Benchmark: decoded information Gbit/s of BP polar decoding on GB300.
+
+Workload (one step = one pass of the whole decode path over one batch):
+  (1024, 512) polar code, frozen set from the BEC(0.5) recursion, BPSK over AWGN
+  at Eb/N0 = 3.0 dB (the operating point of the paper's Sec. IV comparison),
+  2^20 codewords per step per GPU, scaled min-sum alpha = 0.9375, at most 60
+  iterations, G-matrix early stop + CSFG freezing, binary32 messages.
+The same batch is also decoded with fixed iterations and with the G-matrix stop
+alone; FER (95% Wilson interval), average iterations and PE updates per
+codeword are reported for all three.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank decodes its own codewords (weak scaling); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "info Gbit/s/GB300 at N=1024,R=1/2 vs plain BP at equal FER; PE updates/codeword"
+N, K = 1024, 512
+ALPHA = 0.9375
+EBN0 = 3.0
+MAX_ITER = 60
+SEED = 1505049790
+# Issue-slot ceiling of the PE update: 152 SMs x 128 lanes x 2070 MHz, 15 lane
+# instructions per PE (3 adds, 3 min-magnitude selections, 3 scalings by alpha,
+# 6 sign operations); see the design notes.
+SMS, LANES, SM_MAX_HZ, OPS_PER_PE = 152, 128, 2.07e9, 15
+PEAK_PE_PER_S = SMS * LANES * SM_MAX_HZ / OPS_PER_PE
+MODES = {"fixed": (0, 0), "gstop": (1, 0), "gstop_freeze": (1, 1)}
+PROFILE = os.path.join(ROOT, "profiles", "bp_decode_n1024_ebn0_3db.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1505_04979_gb300", "csrc", "bp_decode.cuh")
+
+
+def wilson(k: int, n: int, z: float = 1.96):
+    if n == 0:
+        return (0.0, 1.0)
+    p = k / n
+    d = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return (max(0.0, c - h), min(1.0, c + h))
+
+
+def kernel_traffic():
+    """DRAM bytes per full launch from the committed ncu summary, or None when the
+    kernel source changed since that capture."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_tr:
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    return float(m_tr.group(1)) if sha == m_sha.group(1) else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(gpus: int):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(v, dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.tolist()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_inputs(count: int, first: int):
+    from oracle import oracle as O
+    from paper_1505_04979_gb300 import inputs as I
+    fz = O.bec_frozen(N, K)
+    idx = np.arange(first, first + count)
+    u = I.info_bits(SEED, idx, fz)
+    x = O.encode(u)
+    llr = I.channel_llr(x, I.gaussian(SEED, idx, N), I.sigma(EBN0, K / N))
+    return fz, u, llr
+
+
+def oracle_time(count: int, first: int = 0):
+    from oracle import oracle as O
+    fz, u, llr = oracle_inputs(count, first)
+    t0 = time.perf_counter()
+    uh, it, pe, _ = O.decode_batch(fz, llr, MAX_ITER, ALPHA, 1, 1)
+    dt = time.perf_counter() - t0
+    return dt, uh, u, it, pe
+
+
+def cpu_baseline(target_s: float = 12.0):
+    from oracle import oracle as O
+    O.build()
+    dt, *_ = oracle_time(256, first=1 << 40)
+    rate = 256 / max(dt, 1e-6)
+    count = int(min(60000, max(512, rate * target_s)))
+    dt, uh, u, it, pe = oracle_time(count, first=1 << 40)
+    value = count * K / dt / 1e9
+    return {"value": value, "unit": "Gbit/s", "cores": O.max_threads(), "kind": "oracle",
+            "sample": (f"{count} codewords of the same workload ((1024,512), 3.0 dB, G-matrix stop + CSFG "
+                       f"freezing, max 60 iterations), FP64 oracle threaded over codewords, {dt:.1f} s"),
+            "avg_iters": float(it.mean())}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    dt, *_ = oracle_time(128, first=1 << 41)
+    rate = 128 / max(dt, 1e-6)
+    per_step = int(min(4096, max(64, rate * 4.0)))
+    total_t, total_cw = 0.0, 0
+    for s in range(args.warmup + args.steps):
+        dt, *_ = oracle_time(per_step, first=(1 << 41) + s * per_step)
+        if s >= args.warmup:
+            total_t += dt
+            total_cw += per_step
+    value = total_cw * K / total_t / 1e9
+    cores = O.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(per_step),
+            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} codewords per step of the same workload on {cores} host threads"},
+            "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(batch: int):
+    return {"workload": (f"polar ({N},{K}) BP decoding, BPSK/AWGN Eb/N0 {EBN0} dB, {batch} codewords per step "
+                         f"per GPU, scaled min-sum alpha {ALPHA}, max {MAX_ITER} iterations, G-matrix stop + CSFG "
+                         "freezing"),
+            "N": N, "K": K, "ebn0_db": EBN0, "codewords_per_step": batch, "max_iter": MAX_ITER, "alpha": ALPHA,
+            "frozen_set": "BEC(0.5) Bhattacharyya", "l2": "inputs larger than L2 (4 B x N per codeword), no flush"}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def time_mode(B, code, llr, outs, mode, steps, warmup, stream):
+    import torch
+    uh, it, pe = outs
+    for _ in range(warmup):
+        B.polarbp_decode(code, llr, MAX_ITER, ALPHA, *mode, uh, it, pe, stream=stream)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        B.polarbp_decode(code, llr, MAX_ITER, ALPHA, *mode, uh, it, pe, stream=stream)
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e)
+
+
+def run_ours(args):
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    rank, local, world = dist_setup(args.gpus)
+    if world == 1:
+        build.build()
+    else:
+        if rank == 0:
+            build.build()
+        barrier(world)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    batch = args.batch
+    code = B.polarbp_construct(N, K)
+    first = rank * batch
+    u, llr = B.polarbp_awgn(code, SEED, first, batch, EBN0)
+    uh = torch.empty((batch, N), dtype=torch.uint8, device="cuda")
+    it = torch.empty(batch, dtype=torch.int32, device="cuda")
+    pe = torch.empty(batch, dtype=torch.int64, device="cuda")
+    outs = (uh, it, pe)
+    main = MODES["gstop_freeze"]
+
+    # warm-up, then the timed steps of the headline mode
+    for _ in range(args.warmup):
+        B.polarbp_decode(code, llr, MAX_ITER, ALPHA, *main, uh, it, pe, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            B.polarbp_decode(code, llr, MAX_ITER, ALPHA, *main, uh, it, pe, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
+    ms_step = ms_total / args.steps
+    gpu_launches = args.steps
+
+    per_mode = {}
+    stats_local = {}
+    for name, mode in MODES.items():
+        if name == "gstop_freeze":
+            ms = ms_step
+        elif args.only_main:
+            continue
+        else:
+            ms = time_mode(B, code, llr, outs, mode, args.mode_steps, 1, stream) / args.mode_steps
+            ms = max_over_ranks(ms, world)
+        B.polarbp_decode(code, llr, MAX_ITER, ALPHA, *mode, uh, it, pe, stream=stream)
+        torch.cuda.synchronize()
+        errs = int((uh != u).any(dim=1).sum().item())
+        bit_errs = int((uh != u).sum().item())
+        sums = sum_over_ranks([errs, bit_errs, float(it.double().sum().item()), float(pe.double().sum().item())],
+                              world)
+        n_cw = batch * world
+        fer = sums[0] / n_cw
+        lo, hi = wilson(int(sums[0]), n_cw)
+        pe_cw = sums[3] / n_cw
+        gbit = n_cw * K / (ms * 1e-3) / 1e9
+        pe_rate = n_cw * pe_cw / (ms * 1e-3)
+        per_mode[name] = {"info_gbit_s": gbit, "ms_per_step": ms, "fer": fer, "fer_ci95": [lo, hi],
+                          "ber": sums[1] / (n_cw * K), "avg_iters": sums[2] / n_cw, "pe_per_codeword": pe_cw,
+                          "pe_per_s": pe_rate, "alu_frac": pe_rate / world / PEAK_PE_PER_S}
+        stats_local[name] = pe_cw
+
+    # end-to-end through the host entry point: H2D of the LLRs and D2H of the results every step
+    e2e = None
+    if not args.skip_e2e:
+        h_llr = torch.empty((batch, N), dtype=torch.float32, pin_memory=True)
+        h_llr.copy_(llr)
+        h_u = torch.empty((batch, N), dtype=torch.uint8).pin_memory()
+        h_it = torch.empty(batch, dtype=torch.int32).pin_memory()
+        h_pe = torch.empty(batch, dtype=torch.int64).pin_memory()
+        ws = torch.empty(B.polarbp_decode_host_workspace(code, batch), dtype=torch.uint8, device="cuda")
+        e2e_steps = max(1, min(args.steps, 5))
+        B.polarbp_decode_host(code, h_llr, MAX_ITER, ALPHA, *main, h_u, h_it, h_pe, ws, stream=stream)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            B.polarbp_decode_host(code, h_llr, MAX_ITER, ALPHA, *main, h_u, h_it, h_pe, ws, stream=stream)
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        gpu_launches += e2e_steps
+        e2e = {"value": batch * world * K * e2e_steps / dt / 1e9, "unit": "Gbit/s",
+               "h2d_bytes_per_step": batch * N * 4, "d2h_bytes_per_step": batch * (N + 4 + 8),
+               "steps": e2e_steps, "entry_point": "polarbp_decode_host"}
+        del h_llr, h_u, h_it, h_pe, ws
+
+    if rank != 0:
+        return 0
+    head = per_mode["gstop_freeze"]
+    achieved = head["pe_per_s"] / world
+    traffic = kernel_traffic()
+    line = {
+        "metric": METRIC, "value": head["info_gbit_s"], "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(batch),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": PEAK_PE_PER_S / 1e9, "unit": "GPE/s",
+                     "frac": achieved / PEAK_PE_PER_S,
+                     "traffic": None if traffic is None else traffic,
+                     "kernel": "bp_decode_kernel<10, GSTOP, FREEZE>",
+                     "peak_basis": (f"{SMS} SMs x {LANES} lanes x {SM_MAX_HZ / 1e6:.0f} MHz / {OPS_PER_PE} "
+                                    "lane instructions per PE update"),
+                     "algorithmic_bytes_per_launch": batch * (4 * N + N + 12)},
+        "modes": per_mode,
+        "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if world == 1 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=1 << 20, help="codewords per step per GPU")
+    ap.add_argument("--mode-steps", type=int, default=3, help="timed steps of each comparison mode")
+    ap.add_argument("--only-main", action="store_true", help="skip the comparison modes")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * polarbp.h -- C ABI of the GB300 belief-propagation polar decoder.
+ *
+ * Method: S. M. Abbas, Y. Fan, J. Chen, C.-Y. Tsui, "Low Complexity Belief
+ * Propagation Polar Code Decoder", arXiv 1505.04979.
+ *
+ * Conventions shared by every entry point:
+ *   - N = 2^m code length, K information bits; the frozen set A^c has N-K
+ *     positions (Sec. II).
+ *   - Device pointers are CUDA global-memory pointers the caller allocated on
+ *     the current device; the library never frees them.  Host pointers are
+ *     plain host memory (pinned memory makes the copies asynchronous).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Device-side work is asynchronous on that stream unless an entry
+ *     point says it synchronises.
+ *   - Every call returns a polarbp_status; nothing throws across the ABI.  The
+ *     message of the last failure on the calling thread is in
+ *     polarbp_last_error().
+ *   - Layouts are row-major: [batch][N] for per-position arrays, [batch] for
+ *     per-codeword scalars.  Bits are one byte each (0 or 1).
+ */
+#ifndef POLARBP_H
+#define POLARBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum polarbp_status {
+    POLARBP_OK = 0,
+    POLARBP_ERR_ARG = 1,         /* an argument is out of range or NULL where not allowed */
+    POLARBP_ERR_NONFINITE = 2,   /* a decode saw a NaN or infinite channel LLR */
+    POLARBP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    POLARBP_ERR_TIMEOUT = 4,     /* a device-side bounded wait gave up */
+    POLARBP_ERR_NOMEM = 5,       /* a library allocation failed */
+    POLARBP_ERR_UNSUPPORTED = 6  /* valid arguments this build has no kernel for */
+} polarbp_status;
+
+typedef enum polarbp_stop_mode {
+    POLARBP_STOP_NONE = 0,    /* run exactly max_iter iterations (baseline BP)            */
+    POLARBP_STOP_GMATRIX = 1  /* stop once u_hat G == x_hat (the G-matrix early stop, Sec. I) */
+} polarbp_stop_mode;
+
+typedef enum polarbp_freeze_mode {
+    POLARBP_FREEZE_OFF = 0,  /* every PE of every stage runs every iteration */
+    POLARBP_FREEZE_CSFG = 1  /* connected-sub-factor-graph freezing, Sec. III */
+} polarbp_freeze_mode;
+
+/* Opaque code handle: the frozen set plus its device-side tables.  Owned by the
+ * library; create with polarbp_construct, release with polarbp_destroy. */
+typedef struct polarbp_code polarbp_code;
+
+/*
+ * polarbp_construct -- build an (N, K) polar code (Sec. II).
+ *   N            code length, a power of two, 2 <= N <= 32768.
+ *   K            number of information bits, 0 <= K <= N.
+ *   frozen_mask  host array of N bytes, 1 = frozen, or NULL.  With NULL the
+ *                frozen set is the N-K least reliable synthetic channels of a
+ *                binary erasure channel with erasure probability z0 (the
+ *                Bhattacharyya recursion; the paper does not state its
+ *                construction).  When given, its popcount must be N-K.
+ *   z0           erasure probability in (0, 1); ignored when frozen_mask != NULL.
+ *   out          receives the handle.
+ * Allocates the handle and a few KB of device memory on the current device.
+ * Errors: POLARBP_ERR_ARG, POLARBP_ERR_NOMEM, POLARBP_ERR_CUDA.
+ */
+int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polarbp_code** out);
+
+/*
+ * polarbp_frozen_set -- host-only: the frozen set polarbp_construct builds when
+ * it is given no mask (N-K least reliable BEC(z0) synthetic channels, Sec. II).
+ * frozen_mask receives N bytes (1 = frozen).  Touches no GPU.
+ * Errors: POLARBP_ERR_ARG.
+ */
+int polarbp_frozen_set(int N, int K, double z0, uint8_t* frozen_mask);
+
+/* polarbp_destroy -- release a handle (NULL is ignored).  Synchronises the
+ * device before freeing its tables. */
+void polarbp_destroy(polarbp_code* code);
+
+/* polarbp_code_info -- N, K and m = log2 N of a handle (any out pointer may be NULL). */
+int polarbp_code_info(const polarbp_code* code, int* N, int* K, int* m);
+
+/* polarbp_get_frozen_mask -- copy the frozen set to a host array of N bytes (1 = frozen). */
+int polarbp_get_frozen_mask(const polarbp_code* code, uint8_t* frozen_mask);
+
+/*
+ * polarbp_encode -- x = u F^{(x)m} over GF(2), natural index order (Sec. II, Fig. 1).
+ *   u  device [batch][N] source bits (frozen positions are not forced to 0).
+ *   x  device [batch][N] codeword bits; may not alias u.
+ * Errors: POLARBP_ERR_ARG, POLARBP_ERR_CUDA.
+ */
+int polarbp_encode(const polarbp_code* code, const uint8_t* u, uint8_t* x, int batch, void* stream);
+
+/*
+ * polarbp_decode -- scaled min-sum belief-propagation decoding on the m-stage
+ * factor graph (Sec. II-A, Eq. (1)): one left-to-right sweep of PE stages per
+ * iteration, R messages of the current and L messages of the previous
+ * iteration, L initialised to 0 inside the graph and to the prior (+inf on
+ * frozen positions, 0 elsewhere) on the source side.
+ *   llr          device [batch][N] channel LLRs, log P(x=0)/P(x=1), binary32.
+ *   batch        number of codewords, >= 0 (0 is a no-op).
+ *   max_iter     iteration cap, >= 1.
+ *   scale        the min-sum scaling alpha (0.9375 in Sec. IV), finite and > 0.
+ *   stop_mode    POLARBP_STOP_NONE or POLARBP_STOP_GMATRIX: after every
+ *                iteration, stop when u_hat . F^{(x)m} equals HD(R + L) on the
+ *                channel side; u_hat takes HD(R + L) on the source side, 0 on
+ *                frozen positions and the stored decision on frozen CSFGs.
+ *   freeze_mode  POLARBP_FREEZE_OFF or POLARBP_FREEZE_CSFG (Sec. III): after PE
+ *                stage j-1 the first not-yet-covered CSFG of stage j is checked
+ *                with Eqs. (2)-(4); when it passes, its decision is stored, its
+ *                right-to-left messages are fixed to (-1)^x_hat * inf, and its
+ *                PEs are skipped from then on.  A CSFG whose two halves are
+ *                covered is frozen too.  Decoding ends once every position is
+ *                covered, at the G-matrix stop, or at max_iter.
+ *   u_hat        device [batch][N] decoded source bits (0 on frozen positions).
+ *   iterations   device [batch] int32 iterations run, or NULL.
+ *   pe_updates   device [batch] int64 PE updates executed, counted as in
+ *                Sec. IV (each active PE of each iteration counts once), or NULL.
+ * Supported N: 2..4096 (one codeword per thread block, messages on chip).
+ * A NaN or infinite LLR is recorded in the handle's status word; read it with
+ * polarbp_get_status.  Errors: POLARBP_ERR_ARG, POLARBP_ERR_UNSUPPORTED,
+ * POLARBP_ERR_CUDA (launch failure).
+ */
+int polarbp_decode(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
+                   int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates,
+                   void* stream);
+
+/*
+ * polarbp_decode_trace -- polarbp_decode plus the message planes after every
+ * iteration, for checking against a reference implementation.  Same
+ * arguments, plus device buffers:
+ *   trace_L, trace_R  [batch][max_iter][m+1][N] binary32: L and R of node
+ *                     columns 0..m (column 0 = channel side) at the end of each
+ *                     iteration.  Entries inside covered CSFGs are unspecified.
+ *                     Iterations after the stop are left untouched.
+ *   trace_P           [batch][max_iter] int32: length of the covered prefix of
+ *                     source positions at the end of each iteration.
+ * Slow (every message goes to global memory); N <= 4096.
+ */
+int polarbp_decode_trace(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
+                         int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,
+                         int64_t* pe_updates, float* trace_L, float* trace_R, int32_t* trace_P, void* stream);
+
+/*
+ * polarbp_decode_host_workspace -- bytes of device workspace polarbp_decode_host
+ * needs for `batch` codewords (256-byte aligned sub-buffers).
+ */
+size_t polarbp_decode_host_workspace(const polarbp_code* code, int batch);
+
+/*
+ * polarbp_decode_host -- end-to-end decode from host buffers: copies llr to
+ * the device workspace, decodes as polarbp_decode, copies u_hat, iterations
+ * and pe_updates back, and synchronises `stream` before returning.
+ *   llr, u_hat, iterations, pe_updates  host arrays with the layouts above
+ *                                       (iterations / pe_updates may be NULL).
+ *   workspace        device buffer of at least
+ *                    polarbp_decode_host_workspace(code, batch) bytes.
+ * The library allocates nothing.  Errors as polarbp_decode.
+ */
+int polarbp_decode_host(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
+                        int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,
+                        int64_t* pe_updates, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * polarbp_awgn -- seeded synthetic channel input on the device: the setting of
+ * Sec. IV (BPSK over AWGN).  For codeword c = first_codeword + b (b < batch):
+ * uniform source bits (0 on frozen positions), x = u F^{(x)m}, BPSK 0 -> +1,
+ * 1 -> -1, Gaussian noise of variance sigma^2 = 1 / (2 (K/N) 10^(EbN0/10)),
+ * LLR = 2 y / sigma^2 in binary32.  Random words come from Philox4x32-10
+ * (Salmon et al., SC'11) with key = seed and counter = (block, c low 32 bits,
+ * c high 32 bits, stream), stream 1 for source bits (bit i = bit i%32 of word
+ * i/32) and stream 2 for noise (Box-Muller on words 2p, 2p+1 for positions 2p,
+ * 2p+1), so any codeword can be regenerated on its own.
+ *   u    device [batch][N] source bits, or NULL.
+ *   llr  device [batch][N] channel LLRs.
+ * Requires K >= 1.  Errors: POLARBP_ERR_ARG, POLARBP_ERR_CUDA.
+ */
+int polarbp_awgn(const polarbp_code* code, uint64_t seed, uint64_t first_codeword, int batch, float ebn0_db,
+                 uint8_t* u, float* llr, void* stream);
+
+/*
+ * polarbp_get_status -- read and clear the handle's device status word.  Waits
+ * for `stream`.  Returns POLARBP_ERR_NONFINITE when a decode since the last
+ * call saw a non-finite LLR, else POLARBP_OK (or POLARBP_ERR_CUDA).
+ */
+int polarbp_get_status(const polarbp_code* code, void* stream);
+
+/* polarbp_last_error -- message of the calling thread's last failure ("" if none). */
+const char* polarbp_last_error(void);
+
+/* polarbp_version -- library version string. */
+const char* polarbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLARBP_H */

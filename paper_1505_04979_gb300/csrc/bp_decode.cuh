@@ -1,0 +1,676 @@
+// bp_decode.cuh -- min-sum BP decoding of polar codes with the G-matrix stop
+// and connected-sub-factor-graph (CSFG) freezing, one codeword per thread block.
+//
+// Method: arXiv 1505.04979.  Eq. (1) (Sec. II-A) is the PE update; Sec. III and
+// Eqs. (2)-(4) define the CSFG check, the freezing order and the +-inf feedback;
+// Sec. IV defines the PE-update count.
+//
+// Layout of one decode (N = 2^M, node columns c = 0..M, column 0 = channel side):
+//   * Each worker thread owns EL = 8 elements (all N when N < 8).  The M PE
+//     stages are grouped into phases of up to three stages; in phase p a thread
+//     owns the 8 indices that differ in the phase's three "register bits", so
+//     those stages run entirely in registers (a radix-8 butterfly).
+//   * L columns that are read and written inside one phase live in registers
+//     for the whole decode.  The column between two phases (c = 3, 6, 9, ...)
+//     lives in shared memory, as does the R column when it changes owner at a
+//     phase boundary (double-buffered, one barrier per boundary).
+//   * R is updated in place: stage s turns R[s] into R[s+1] pairwise.
+//   * Freezing state is a single integer P: the covered source positions always
+//     form the prefix [0, P) (the checked CSFG is the first uncovered one of its
+//     stage and covered CSFGs never shrink), so "level-s CSFG of index a is
+//     covered" is  a < (P >> (M-s)) << (M-s).
+//   * The sweep records hard decisions of the R columns the checks need; after
+//     the sweep one warp runs the checks of stages 1..M in order, the G-matrix
+//     test and the termination decision.  Running the checks after the sweep
+//     gives the same messages as running each right after its stage: a check at
+//     stage j only reads R[j], only changes L[j] (and enclosing CSFGs' L) of
+//     blocks it covers, and those messages are next read in the following
+//     iteration; PEs it would have skipped in the rest of the sweep only write
+//     messages of covered CSFGs, which nothing reads again.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace polarbp {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+template <int M_>
+struct Geo {
+    static constexpr int M = M_;
+    static constexpr int N = 1 << M;
+    static constexpr int RB = M < 3 ? M : 3;   // register bits per thread
+    static constexpr int EL = 1 << RB;         // elements per thread
+    static constexpr int T = N / EL;           // worker threads
+    static constexpr int NP = (M + 2) / 3;     // phases
+    static constexpr int BLOCK = T < 32 ? 32 : T;
+    static constexpr int NW = N < 32 ? 1 : N / 32;  // 32-bit words of an N-bit vector
+    static constexpr int NB = (M - 1) / 3;          // shared-memory L columns
+    static constexpr int MIN_BLOCKS = (640 / BLOCK) < 1 ? 1 : (640 / BLOCK);
+
+    __host__ __device__ static constexpr int s0(int p) { return 3 * p; }
+    __host__ __device__ static constexpr int cnt(int p) { return (M - 3 * p) < 3 ? (M - 3 * p) : 3; }
+    __host__ __device__ static constexpr int lo(int p) { return (p == NP - 1) ? 0 : (M - 3 - 3 * p); }
+    __host__ __device__ static constexpr bool is_boundary(int c) { return c > 0 && c < M && (c % 3) == 0; }
+    __host__ __device__ static constexpr bool is_reg(int c) { return c > 0 && c <= M && !is_boundary(c); }
+    __host__ __device__ static constexpr int bslot(int c) { return c / 3 - 1; }
+    __host__ __device__ static constexpr int rslot(int c)
+    {
+        int r = 0;
+        for (int x = 1; x < c; ++x) r += is_reg(x) ? 1 : 0;
+        return r;
+    }
+    static constexpr int NR = M - NB;  // register columns
+    __host__ __device__ static constexpr int owner(int c) { return (c / 3) < (NP - 1) ? (c / 3) : (NP - 1); }
+};
+
+// Global index of element e of thread t in phase PH's mapping: the phase's
+// register bits come from e, the other bits (ascending) from t.
+template <int M, int PH>
+__device__ __forceinline__ int elem_index(int t, int e)
+{
+    constexpr int lo = Geo<M>::lo(PH);
+    constexpr int RB = Geo<M>::RB;
+    return (t & ((1 << lo) - 1)) | (e << lo) | ((t >> lo) << (lo + RB));
+}
+
+// XOR swizzle of float arrays in shared memory (stays inside each 32-entry row).
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 31); }
+
+// alpha * sign(x) sign(y) min(|x|, |y|)  (Eq. (1)).  The magnitude is exact,
+// the product by alpha rounds once; the sign bit is xor-ed in.
+__device__ __forceinline__ float fms(float x, float y, float alpha)
+{
+    const float mag = __fmul_rn(alpha, fminf(fabsf(x), fabsf(y)));
+    const uint32_t s = (__float_as_uint(x) ^ __float_as_uint(y)) & 0x80000000u;
+    return __uint_as_float(__float_as_uint(mag) | s);
+}
+
+struct DecodeArgs {
+    const float* llr;
+    const uint32_t* frozen_words;  // NW words, bit i of word i/32 = frozen[i]
+    uint8_t* u_hat;
+    int32_t* iters;
+    int64_t* pe;
+    unsigned int* status;
+    float* trace_L;
+    float* trace_R;
+    int32_t* trace_P;
+    int batch;
+    int max_iter;
+    float alpha;
+};
+
+enum : int { CTL_P = 0, CTL_DONE = 1, CTL_EVENT = 2, CTL_PE = 4, CTL_EV = 8 };
+
+template <int M>
+struct SmemLayout {
+    using G = Geo<M>;
+    static constexpr int N = G::N, NW = G::NW;
+    static constexpr size_t off_Lb = 0;
+    static constexpr size_t off_Rx = off_Lb + sizeof(float) * G::NB * N;
+    static constexpr size_t off_U = off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * N;
+    static constexpr size_t off_Fz = off_U + sizeof(uint32_t) * NW;
+    static constexpr size_t off_Xf = off_Fz + sizeof(uint32_t) * NW;
+    static constexpr size_t off_Ctl = (off_Xf + sizeof(uint32_t) * (M + 1) * NW + 15) / 16 * 16;
+    static constexpr int CTL_INTS = CTL_EV + 2 * (M + 1);
+    static constexpr size_t off_Hd = (off_Ctl + sizeof(int) * CTL_INTS + 15) / 16 * 16;
+    static constexpr size_t hd_bytes = (size_t)(M + 1) * N;
+    static constexpr size_t bytes = (off_Hd + hd_bytes + 15) / 16 * 16;
+};
+
+template <int M>
+struct Smem {
+    float* Lb;
+    float* Rx;
+    uint32_t* U;    // stored source bits of covered positions
+    uint32_t* Fz;   // frozen mask
+    uint32_t* Xf;   // [(M+1)][NW] hard decisions of the latest feedback event per column
+    int* ctl;
+    uint8_t* hd;    // [(M+1)][N] hard-decision snapshots (0/1 bytes)
+    __device__ __forceinline__ explicit Smem(unsigned char* base)
+    {
+        using L = SmemLayout<M>;
+        Lb = reinterpret_cast<float*>(base + L::off_Lb);
+        Rx = reinterpret_cast<float*>(base + L::off_Rx);
+        U = reinterpret_cast<uint32_t*>(base + L::off_U);
+        Fz = reinterpret_cast<uint32_t*>(base + L::off_Fz);
+        Xf = reinterpret_cast<uint32_t*>(base + L::off_Xf);
+        ctl = reinterpret_cast<int*>(base + L::off_Ctl);
+        hd = base + L::off_Hd;
+    }
+    __device__ __forceinline__ long long* pe_acc() { return reinterpret_cast<long long*>(ctl + CTL_PE); }
+    __device__ __forceinline__ int* ev_lo() { return ctl + CTL_EV; }
+    __device__ __forceinline__ int* ev_hi() { return ctl + CTL_EV + (M + 1); }
+};
+
+__device__ __forceinline__ uint32_t bit_of(const uint32_t* words, int i) { return (words[i >> 5] >> (i & 31)) & 1u; }
+
+// ---------------------------------------------------------------------------
+// warp-level bit-vector helpers for the checks (word w = 32 r + lane)
+// ---------------------------------------------------------------------------
+template <int S>
+struct BlockBits {
+    static constexpr int W = S >= 32 ? S / 32 : 1;
+    static constexpr int R = (W + 31) / 32;
+};
+
+// four 0/1 bytes of a word -> 4 bits (byte k -> bit k)
+__device__ __forceinline__ uint32_t nib4(uint32_t w) { return (w * 0x01020408u) >> 24; }
+
+__device__ __forceinline__ uint32_t pack32(const uint8_t* p32)
+{
+    const uint4 a = reinterpret_cast<const uint4*>(p32)[0];
+    const uint4 b = reinterpret_cast<const uint4*>(p32)[1];
+    return nib4(a.x) | (nib4(a.y) << 4) | (nib4(a.z) << 8) | (nib4(a.w) << 12) | (nib4(b.x) << 16) |
+           (nib4(b.y) << 20) | (nib4(b.z) << 24) | (nib4(b.w) << 28);
+}
+
+// S hard-decision bytes at hd[base..base+S) -> packed words
+template <int S>
+__device__ __forceinline__ void hd_load(const uint8_t* hd, int base, uint32_t (&v)[BlockBits<S>::R], int lane)
+{
+    if constexpr (S >= 32) {
+#pragma unroll
+        for (int r = 0; r < BlockBits<S>::R; ++r) {
+            const int w = 32 * r + lane;
+            v[r] = (w < BlockBits<S>::W) ? pack32(hd + base + 32 * w) : 0u;
+        }
+    } else {
+        const bool b = (lane < S) ? (hd[base + lane] != 0) : false;
+        v[0] = __ballot_sync(kFull, b);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void packed_load(const uint32_t* words, int base, uint32_t (&v)[BlockBits<S>::R],
+                                            int lane)
+{
+    if constexpr (S >= 32) {
+#pragma unroll
+        for (int r = 0; r < BlockBits<S>::R; ++r) {
+            const int w = 32 * r + lane;
+            v[r] = (w < BlockBits<S>::W) ? words[(base >> 5) + w] : 0u;
+        }
+    } else {
+        v[0] = (words[base >> 5] >> (base & 31)) & ((1u << S) - 1u);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void packed_store(uint32_t* words, int base, const uint32_t (&v)[BlockBits<S>::R],
+                                             int lane)
+{
+    if constexpr (S >= 32) {
+#pragma unroll
+        for (int r = 0; r < BlockBits<S>::R; ++r) {
+            const int w = 32 * r + lane;
+            if (w < BlockBits<S>::W) words[(base >> 5) + w] = v[r];
+        }
+    } else {
+        if (lane == 0) {
+            const uint32_t mask = ((1u << S) - 1u) << (base & 31);
+            uint32_t* p = words + (base >> 5);
+            *p = (*p & ~mask) | ((v[0] << (base & 31)) & mask);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t xmask(int h)
+{
+    return h == 1 ? 0x55555555u : h == 2 ? 0x33333333u : h == 4 ? 0x0F0F0F0Fu : h == 8 ? 0x00FF00FFu : 0x0000FFFFu;
+}
+
+// v <- v . F^{(x) log2 S}: for every bit h of the position, entries with bit h
+// clear absorb (xor) the entry with bit h set.
+template <int S>
+__device__ __forceinline__ void polar_xform(uint32_t (&v)[BlockBits<S>::R], int lane)
+{
+    constexpr int R = BlockBits<S>::R;
+    constexpr int INW = S < 32 ? S : 32;
+#pragma unroll
+    for (int h = 1; h < INW; h <<= 1) {
+        const uint32_t mk = xmask(h);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] ^= (v[r] >> h) & mk;
+    }
+    if constexpr (S > 32) {
+        constexpr int W = BlockBits<S>::W;
+#pragma unroll
+        for (int d = 1; d < W; d <<= 1) {
+            if (d < 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t y = __shfl_down_sync(kFull, v[r], d);
+                    if ((lane & d) == 0) v[r] ^= y;
+                }
+            } else {
+                const int dr = d / 32;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if ((r & dr) == 0) v[r] ^= v[r + dr];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// checker warp
+// ---------------------------------------------------------------------------
+// After a freeze that ended at P, freeze every enclosing CSFG that has become
+// fully covered: its hard decision is its stored source bits re-encoded.
+template <int M, int JP>
+__device__ __forceinline__ void propagate(Smem<M>& sm, int P, int lane)
+{
+    if constexpr (JP >= 1) {
+        constexpr int Sp = Geo<M>::N >> JP;
+        constexpr int NW = Geo<M>::NW;
+        if ((P & (Sp - 1)) == 0) {
+            const int bp = P - Sp;
+            uint32_t v[BlockBits<Sp>::R];
+            packed_load<Sp>(sm.U, bp, v, lane);
+            polar_xform<Sp>(v, lane);
+            packed_store<Sp>(sm.Xf + JP * NW, bp, v, lane);
+            if (lane == 0) {
+                sm.ev_lo()[JP] = bp;
+                sm.ev_hi()[JP] = P;
+                sm.ctl[CTL_EVENT] = 1;
+            }
+            __syncwarp();
+            propagate<M, JP - 1>(sm, P, lane);
+        }
+    }
+}
+
+// Eqs. (2)-(4) on the first uncovered CSFG of stage J.
+template <int M, int J>
+__device__ __forceinline__ void check_level(Smem<M>& sm, int& P, int lane)
+{
+    constexpr int N = Geo<M>::N;
+    constexpr int S = N >> J;
+    constexpr int R = BlockBits<S>::R;
+    constexpr int NW = Geo<M>::NW;
+    if (P >= N) return;
+    const int base = (P >> (M - J)) << (M - J);
+    uint32_t x[R], u[R], f[R];
+    hd_load<S>(sm.hd + J * N, base, x, lane);  // Eq. (2)
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = x[r];
+    polar_xform<S>(u, lane);                    // Eq. (3)
+    packed_load<S>(sm.Fz, base, f, lane);
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) bad |= (u[r] & f[r]) != 0u;
+    if (__any_sync(kFull, bad)) return;         // Eq. (4) fails
+    packed_store<S>(sm.U, base, u, lane);
+    packed_store<S>(sm.Xf + J * NW, base, x, lane);
+    if (lane == 0) {
+        sm.ev_lo()[J] = base;
+        sm.ev_hi()[J] = base + S;
+        sm.ctl[CTL_EVENT] = 1;
+    }
+    P = base + S;
+    __syncwarp();
+    propagate<M, J - 1>(sm, P, lane);
+}
+
+template <int M, int J>
+__device__ __forceinline__ void check_all(Smem<M>& sm, int& P, int& pe_it, int lane)
+{
+    if constexpr (J <= M) {
+        check_level<M, J>(sm, P, lane);
+        if constexpr (J < M) pe_it += (Geo<M>::N - ((P >> (M - J)) << (M - J))) >> 1;
+        check_all<M, J + 1>(sm, P, pe_it, lane);
+    }
+}
+
+// G-matrix stop: u_hat . F^{(x)M} == HD(R[0] + L[0]).
+template <int M>
+__device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
+{
+    constexpr int N = Geo<M>::N;
+    constexpr int R = BlockBits<N>::R;
+    constexpr int NW = Geo<M>::NW;
+    uint32_t u[R], x[R];
+    hd_load<N>(sm.hd + M * N, 0, u, lane);
+    hd_load<N>(sm.hd, 0, x, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int w = (N >= 32) ? 32 * r + lane : 0;
+        uint32_t cov;
+        if (P >= 32 * (w + 1)) cov = kFull;
+        else if (P <= 32 * w) cov = 0u;
+        else cov = (1u << (P - 32 * w)) - 1u;
+        const uint32_t us = (w < NW) ? sm.U[w] : 0u;
+        const uint32_t fz = (w < NW) ? sm.Fz[w] : 0u;
+        u[r] = (us & cov) | (u[r] & ~fz & ~cov);
+    }
+    polar_xform<N>(u, lane);
+    bool same = true;
+    constexpr uint32_t valid = (N >= 32) ? kFull : ((1u << (N & 31)) - 1u);
+#pragma unroll
+    for (int r = 0; r < R; ++r) same &= ((u[r] ^ x[r]) & valid) == 0u;
+    return __all_sync(kFull, same);
+}
+
+template <int M, bool GSTOP, bool FREEZE>
+__device__ __noinline__ void checker(unsigned char* smem_base, int lane)
+{
+    constexpr int N = Geo<M>::N;
+    Smem<M> sm(smem_base);
+    if (lane <= M) {
+        sm.ev_lo()[lane] = 0;
+        sm.ev_hi()[lane] = 0;
+    }
+    if (lane == 0) sm.ctl[CTL_EVENT] = 0;
+    __syncwarp();
+    int P = sm.ctl[CTL_P];
+    int pe_it = N >> 1;  // stage 0 always runs
+    if constexpr (FREEZE) {
+        check_all<M, 1>(sm, P, pe_it, lane);
+    } else {
+        pe_it = M * (N >> 1);
+    }
+    bool done = FREEZE && (P >= N);
+    if constexpr (GSTOP) {
+        if (!done) done = gmatrix_ok<M>(sm, P, lane);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        sm.ctl[CTL_P] = P;
+        sm.ctl[CTL_DONE] = done ? 1 : 0;
+        *sm.pe_acc() += pe_it;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the sweep
+// ---------------------------------------------------------------------------
+template <int M>
+struct Regs {
+    float R[Geo<M>::EL];
+    float Lr[Geo<M>::NR][Geo<M>::EL];
+    float llr[Geo<M>::EL];
+};
+
+template <int M, int C>
+__device__ __forceinline__ float load_L(Regs<M>& rg, Smem<M>& sm, int e, int i)
+{
+    using G = Geo<M>;
+    if constexpr (G::is_boundary(C)) return sm.Lb[G::bslot(C) * G::N + swz(i)];
+    else return rg.Lr[G::rslot(C)][e];
+}
+
+template <int M, int C>
+__device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int i, float v)
+{
+    using G = Geo<M>;
+    if constexpr (C == 0) {
+        (void)rg; (void)sm; (void)e; (void)i; (void)v;
+    } else if constexpr (G::is_boundary(C)) {
+        sm.Lb[G::bslot(C) * G::N + swz(i)] = v;
+    } else {
+        rg.Lr[G::rslot(C)][e] = v;
+    }
+}
+
+template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE>
+__device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha,
+                                          const DecodeArgs& a, long long trace_base)
+{
+    using G = Geo<M>;
+    constexpr int N = G::N, EL = G::EL;
+    constexpr int s = G::s0(PH) + Q;
+    constexpr int b = M - 1 - s;
+    constexpr int k = b - G::lo(PH);
+    constexpr bool snap = FREEZE || (GSTOP && s == M - 1);
+    const int thr = (s == 0) ? 0 : ((P0 >> (M - s)) << (M - s));
+    uint8_t* hd_next = sm.hd + (s + 1) * N;
+#pragma unroll
+    for (int e = 0; e < EL; ++e) {
+        if (e & (1 << k)) continue;
+        const int e2 = e | (1 << k);
+        const int ia = elem_index<M, PH>(tid, e);
+        const int ib = ia + (1 << b);
+        if (ia < thr) continue;  // PE inside a covered CSFG: skipped
+        const float La = load_L<M, s + 1>(rg, sm, e, ia);
+        const float Lb = load_L<M, s + 1>(rg, sm, e2, ib);
+        const float Ra = rg.R[e];
+        const float Rb = rg.R[e2];
+        const float t = __fadd_rn(Lb, Rb);
+        const float g = fms(La, Ra, alpha);
+        const float nLa = fms(La, t, alpha);
+        const float nLb = __fadd_rn(Lb, g);
+        const float nRa = fms(Ra, t, alpha);
+        const float nRb = __fadd_rn(Rb, g);
+        store_L<M, s>(rg, sm, e, ia, nLa);
+        store_L<M, s>(rg, sm, e2, ib, nLb);
+        if constexpr (s == 0 && GSTOP) {
+            sm.hd[ia] = __fadd_rn(Ra, nLa) < 0.f;
+            sm.hd[ib] = __fadd_rn(Rb, nLb) < 0.f;
+        }
+        if constexpr (s == 0 && TRACE) {
+            a.trace_L[trace_base + ia] = nLa;
+            a.trace_L[trace_base + ib] = nLb;
+        }
+        rg.R[e] = nRa;
+        rg.R[e2] = nRb;
+        if constexpr (snap) {
+            hd_next[ia] = nRa < 0.f;
+            hd_next[ib] = nRb < 0.f;
+        }
+    }
+    if constexpr (TRACE) {
+#pragma unroll
+        for (int e = 0; e < EL; ++e)
+            a.trace_R[trace_base + (long long)(s + 1) * N + elem_index<M, PH>(tid, e)] = rg.R[e];
+    }
+    if constexpr (Q + 1 < G::cnt(PH)) run_stage<M, PH, Q + 1, GSTOP, FREEZE, TRACE>(rg, sm, tid, P0, alpha, a, trace_base);
+}
+
+template <int M, int PH, bool GSTOP, bool FREEZE, bool TRACE>
+__device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, int P0, float alpha,
+                                          const DecodeArgs& a, long long trace_base)
+{
+    using G = Geo<M>;
+    constexpr int N = G::N, EL = G::EL;
+    if constexpr (PH > 0) {
+        if (worker) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) rg.R[e] = sm.Rx[((PH - 1) & 1) * N + swz(elem_index<M, PH>(tid, e))];
+        }
+    }
+    if (worker) run_stage<M, PH, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, P0, alpha, a, trace_base);
+    if constexpr (PH + 1 < G::NP) {
+        if (worker) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) sm.Rx[(PH & 1) * N + swz(elem_index<M, PH>(tid, e))] = rg.R[e];
+        }
+        __syncthreads();
+        run_phase<M, PH + 1, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
+    }
+}
+
+// Fix L of the columns that received a freeze event to (-1)^x_hat * inf.
+template <int M, int C>
+__device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, bool worker)
+{
+    using G = Geo<M>;
+    if constexpr (C <= M) {
+        const int lo = sm.ev_lo()[C], hi = sm.ev_hi()[C];
+        if (hi > lo) {
+            const uint32_t* xf = sm.Xf + C * G::NW;
+            if constexpr (G::is_boundary(C)) {
+                for (int i = lo + tid; i < hi; i += blockDim.x)
+                    sm.Lb[G::bslot(C) * G::N + swz(i)] = bit_of(xf, i) ? -INFINITY : INFINITY;
+            } else if (worker) {
+#pragma unroll
+                for (int e = 0; e < G::EL; ++e) {
+                    const int i = elem_index<M, G::owner(C)>(tid, e);
+                    if (i >= lo && i < hi) rg.Lr[G::rslot(C)][e] = bit_of(xf, i) ? -INFINITY : INFINITY;
+                }
+            }
+        }
+        apply_events<M, C + 1>(rg, sm, tid, worker);
+    }
+}
+
+template <int M, int C>
+__device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, const DecodeArgs& a,
+                                                long long trace_base)
+{
+    using G = Geo<M>;
+    if constexpr (C <= M) {
+        if constexpr (G::is_boundary(C)) {
+            for (int i = tid; i < G::N; i += blockDim.x)
+                a.trace_L[trace_base + (long long)C * G::N + i] = sm.Lb[G::bslot(C) * G::N + swz(i)];
+        } else if (worker) {
+#pragma unroll
+            for (int e = 0; e < G::EL; ++e)
+                a.trace_L[trace_base + (long long)C * G::N + elem_index<M, G::owner(C)>(tid, e)] = rg.Lr[G::rslot(C)][e];
+        }
+        trace_L_columns<M, C + 1>(rg, sm, tid, worker, a, trace_base);
+    }
+}
+
+template <int M, bool GSTOP, bool FREEZE, bool TRACE>
+__global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_kernel(DecodeArgs a)
+{
+    using G = Geo<M>;
+    constexpr int N = G::N, EL = G::EL, T = G::T, NW = G::NW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<M> sm(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool worker = tid < T;
+    const long long cw = blockIdx.x;
+    const float alpha = a.alpha;
+
+    for (int w = tid; w < NW; w += blockDim.x) {
+        sm.Fz[w] = a.frozen_words[w];
+        sm.U[w] = 0u;
+    }
+    for (int i = tid; i < G::NB * N; i += blockDim.x) sm.Lb[i] = 0.f;
+    {
+        uint32_t* hd32 = reinterpret_cast<uint32_t*>(sm.hd);
+        for (int i = tid; i < (int)(SmemLayout<M>::hd_bytes / 4); i += blockDim.x) hd32[i] = 0u;
+    }
+    if (tid == 0) {
+        sm.ctl[CTL_P] = 0;
+        sm.ctl[CTL_DONE] = 0;
+        sm.ctl[CTL_EVENT] = 0;
+        *sm.pe_acc() = 0;
+    }
+    __syncthreads();
+
+    Regs<M> rg;
+    if (worker) {
+        bool finite = true;
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            const float v = a.llr[cw * N + elem_index<M, 0>(tid, e)];
+            finite &= isfinite(v);
+            rg.llr[e] = v;
+            rg.R[e] = v;
+        }
+        if (!finite) atomicOr(a.status, 1u);
+#pragma unroll
+        for (int c = 0; c < G::NR; ++c)
+#pragma unroll
+            for (int e = 0; e < EL; ++e) rg.Lr[c][e] = 0.f;
+        // source-side prior (reading: +inf on frozen positions, 0 elsewhere)
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            const int i = elem_index<M, G::NP - 1>(tid, e);
+            rg.Lr[G::rslot(M)][e] = bit_of(sm.Fz, i) ? INFINITY : 0.f;
+        }
+    }
+
+    int it = 1;
+    for (; it <= a.max_iter; ++it) {
+        const int P0 = sm.ctl[CTL_P];
+        const long long trace_base = TRACE ? (cw * a.max_iter + (it - 1)) * (long long)(M + 1) * N : 0;
+        if (worker) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) rg.R[e] = rg.llr[e];
+            if constexpr (TRACE) {
+#pragma unroll
+                for (int e = 0; e < EL; ++e) a.trace_R[trace_base + elem_index<M, 0>(tid, e)] = rg.llr[e];
+            }
+        }
+        run_phase<M, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
+        __syncthreads();
+        if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane);
+        __syncthreads();
+        const bool done = sm.ctl[CTL_DONE] != 0;
+        if constexpr (FREEZE) {
+            if (sm.ctl[CTL_EVENT]) {
+                apply_events<M, 1>(rg, sm, tid, worker);
+                __syncthreads();
+            }
+        }
+        if constexpr (TRACE) {
+            trace_L_columns<M, 1>(rg, sm, tid, worker, a, trace_base);
+            if (tid == 0) a.trace_P[cw * a.max_iter + (it - 1)] = sm.ctl[CTL_P];
+        }
+        if (done) break;
+    }
+    const int iters = it <= a.max_iter ? it : a.max_iter;
+
+    // output: stored bits on covered positions, HD(R[M]) elsewhere, 0 on frozen
+    if (worker) {
+        const int P = sm.ctl[CTL_P];
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            const int i = elem_index<M, G::NP - 1>(tid, e);
+            uint8_t bit;
+            if (i < P) bit = (uint8_t)bit_of(sm.U, i);
+            else bit = bit_of(sm.Fz, i) ? 0 : (rg.R[e] < 0.f ? 1 : 0);
+            a.u_hat[cw * N + i] = bit;
+        }
+    }
+    if (tid == 0) {
+        if (a.iters) a.iters[cw] = iters;
+        if (a.pe) a.pe[cw] = *sm.pe_acc();
+    }
+}
+
+struct LaunchReq {
+    DecodeArgs args;
+    int stop_mode;
+    int freeze_mode;
+    bool trace;
+    cudaStream_t stream;
+};
+
+template <int M, bool GSTOP, bool FREEZE, bool TRACE>
+cudaError_t launch_one(const LaunchReq& q)
+{
+    auto kern = bp_decode_kernel<M, GSTOP, FREEZE, TRACE>;
+    constexpr size_t smem = SmemLayout<M>::bytes;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<q.args.batch, Geo<M>::BLOCK, smem, q.stream>>>(q.args);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_decode(const LaunchReq& q)
+{
+    const bool g = q.stop_mode != 0, f = q.freeze_mode != 0;
+    if (q.trace) {
+        if (g && f) return launch_one<M, true, true, true>(q);
+        if (g) return launch_one<M, true, false, true>(q);
+        if (f) return launch_one<M, false, true, true>(q);
+        return launch_one<M, false, false, true>(q);
+    }
+    if (g && f) return launch_one<M, true, true, false>(q);
+    if (g) return launch_one<M, true, false, false>(q);
+    if (f) return launch_one<M, false, true, false>(q);
+    return launch_one<M, false, false, false>(q);
+}
+
+}  // namespace polarbp

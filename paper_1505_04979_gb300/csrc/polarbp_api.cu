@@ -1,0 +1,463 @@
+// polarbp_api.cu -- host side of the C ABI declared in include/polarbp.h:
+// argument checking, code construction (Sec. II), the encoder kernel and the
+// dispatch of the decode kernels in bp_decode.cuh.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "polarbp.h"
+#include "bp_decode.cuh"
+
+struct polarbp_code {
+    int N = 0, K = 0, m = 0;
+    int device = 0;
+    std::vector<uint8_t> frozen;
+    uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
+    unsigned int* d_status = nullptr;
+};
+
+// decode kernels, one translation unit per code length (compiled in parallel)
+namespace polarbp {
+cudaError_t launch_m1(const LaunchReq&);
+cudaError_t launch_m2(const LaunchReq&);
+cudaError_t launch_m3(const LaunchReq&);
+cudaError_t launch_m4(const LaunchReq&);
+cudaError_t launch_m5(const LaunchReq&);
+cudaError_t launch_m6(const LaunchReq&);
+cudaError_t launch_m7(const LaunchReq&);
+cudaError_t launch_m8(const LaunchReq&);
+cudaError_t launch_m9(const LaunchReq&);
+cudaError_t launch_m10(const LaunchReq&);
+cudaError_t launch_m11(const LaunchReq&);
+cudaError_t launch_m12(const LaunchReq&);
+}  // namespace polarbp
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return POLARBP_ERR_CUDA;
+}
+
+int exact_log2(int n)
+{
+    if (n < 1) return -1;
+    int m = 0;
+    while ((1 << m) < n) ++m;
+    return (1 << m) == n ? m : -1;
+}
+
+// Frozen set of an (N, K) code from the Bhattacharyya parameters of a binary
+// erasure channel with erasure probability z0 (the paper leaves the
+// construction open).  Position i's synthetic channel is obtained by splitting
+// z0 m times, the bits of i from the most significant one down choosing the
+// worse (2z - z^2, bit 0) or the better (z^2, bit 1) half; the pair
+// (ln z, ln(1 - z)) is tracked so neither tail saturates.  The N - K positions
+// with the largest z are frozen; among equal z the smaller index counts as the
+// less reliable.
+void bec_frozen_set(int N, int m, int K, double z0, std::vector<uint8_t>& frozen)
+{
+    std::vector<std::pair<double, int>> order(N);
+    for (int i = 0; i < N; ++i) {
+        double lz = std::log(z0), lw = std::log1p(-z0);  // ln z, ln(1 - z)
+        for (int b = m - 1; b >= 0; --b) {
+            if ((i >> b) & 1) {
+                const double lw_next = lw + std::log1p(std::exp(lz));
+                lz = 2.0 * lz;
+                lw = lw_next;
+            } else {
+                const double lz_next = lz + std::log1p(std::exp(lw));
+                lw = 2.0 * lw;
+                lz = lz_next;
+            }
+        }
+        order[i] = {lz - lw, i};
+    }
+    std::sort(order.begin(), order.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+        if (a.first != b.first) return a.first < b.first;
+        return a.second > b.second;
+    });
+    frozen.assign(N, 1);
+    for (int k = 0; k < K; ++k) frozen[order[k].second] = 0;
+}
+
+int check_device(const polarbp_code* c)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != c->device) return fail(POLARBP_ERR_ARG, "code handle belongs to another device");
+    return POLARBP_OK;
+}
+
+// x = u F^{(x)m}: one block per codeword, the N bits in shared memory, one
+// butterfly pass per index bit (v[c] ^= v[c + h] for c with bit h clear).
+__global__ void encode_kernel(const uint8_t* __restrict__ u, uint8_t* __restrict__ x, int N, int m)
+{
+    extern __shared__ uint8_t buf[];
+    const long long cw = blockIdx.x;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) buf[i] = u[cw * N + i] & 1u;
+    __syncthreads();
+    for (int b = 0; b < m; ++b) {
+        const int h = 1 << b;
+        for (int c = threadIdx.x; c < N; c += blockDim.x)
+            if (!(c & h)) buf[c] ^= buf[c + h];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) x[cw * N + i] = buf[i];
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint64_t cw, uint32_t stream, uint32_t w)
+{
+    const uint4 o = philox4x32_10(make_uint4(w >> 2, (uint32_t)cw, (uint32_t)(cw >> 32), stream), (uint32_t)seed,
+                                  (uint32_t)(seed >> 32));
+    const uint32_t q = w & 3u;
+    return q == 0 ? o.x : q == 1 ? o.y : q == 2 ? o.z : o.w;
+}
+
+// One block per codeword: source bits, encoder (as encode_kernel), BPSK + AWGN.
+__global__ void awgn_kernel(const uint32_t* __restrict__ frozen_words, int N, int m, uint64_t seed, uint64_t first,
+                            float sigma, uint8_t* __restrict__ u_out, float* __restrict__ llr)
+{
+    extern __shared__ uint8_t bits[];
+    const long long b = blockIdx.x;
+    const uint64_t cw = first + (uint64_t)b;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const uint32_t word = philox_word(seed, cw, 1u, (uint32_t)(i >> 5));
+        const uint32_t fz = (frozen_words[i >> 5] >> (i & 31)) & 1u;
+        const uint8_t ui = fz ? 0 : (uint8_t)((word >> (i & 31)) & 1u);
+        bits[i] = ui;
+        if (u_out) u_out[b * N + i] = ui;
+    }
+    __syncthreads();
+    for (int s = 0; s < m; ++s) {
+        const int h = 1 << s;
+        for (int c = threadIdx.x; c < N; c += blockDim.x)
+            if (!(c & h)) bits[c] ^= bits[c + h];
+        __syncthreads();
+    }
+    const float scale = 2.f / (sigma * sigma);
+    for (int p = threadIdx.x; p < (N + 1) / 2; p += blockDim.x) {
+        const uint32_t w0 = philox_word(seed, cw, 2u, (uint32_t)(2 * p));
+        const uint32_t w1 = philox_word(seed, cw, 2u, (uint32_t)(2 * p + 1));
+        const float u1 = ((float)w0 + 1.0f) * 2.3283064365386963e-10f;  // (w0 + 1) / 2^32
+        const float u2 = (float)w1 * 2.3283064365386963e-10f;
+        const float r = sqrtf(-2.f * logf(u1));
+        float sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        const int i0 = 2 * p, i1 = 2 * p + 1;
+        llr[b * N + i0] = scale * ((1.f - 2.f * bits[i0]) + sigma * r * cs);
+        if (i1 < N) llr[b * N + i1] = scale * ((1.f - 2.f * bits[i1]) + sigma * r * sn);
+    }
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct HostLayout {
+    size_t llr, u_hat, iters, pe, total;
+};
+
+HostLayout host_layout(int N, int batch)
+{
+    HostLayout h;
+    size_t b = (size_t)batch;
+    h.llr = 0;
+    h.u_hat = align256(h.llr + b * N * sizeof(float));
+    h.iters = align256(h.u_hat + b * N);
+    h.pe = align256(h.iters + b * sizeof(int32_t));
+    h.total = align256(h.pe + b * sizeof(int64_t));
+    return h;
+}
+
+int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale, int stop_mode,
+                int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates, float* trace_L,
+                float* trace_R, int32_t* trace_P, bool trace, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (max_iter < 1) return fail(POLARBP_ERR_ARG, "max_iter must be >= 1");
+    if (!(scale > 0.f) || !std::isfinite(scale)) return fail(POLARBP_ERR_ARG, "scale must be finite and > 0");
+    if (stop_mode != POLARBP_STOP_NONE && stop_mode != POLARBP_STOP_GMATRIX)
+        return fail(POLARBP_ERR_ARG, "unknown stop_mode");
+    if (freeze_mode != POLARBP_FREEZE_OFF && freeze_mode != POLARBP_FREEZE_CSFG)
+        return fail(POLARBP_ERR_ARG, "unknown freeze_mode");
+    if (batch == 0) return POLARBP_OK;
+    if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be device pointers");
+    if (trace && (!trace_L || !trace_R || !trace_P)) return fail(POLARBP_ERR_ARG, "trace buffers must be given");
+    if (c->m > 12) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 4096 in this build");
+    int rc = check_device(c);
+    if (rc != POLARBP_OK) return rc;
+
+    polarbp::LaunchReq q;
+    q.args.llr = llr;
+    q.args.frozen_words = c->d_frozen;
+    q.args.u_hat = u_hat;
+    q.args.iters = iterations;
+    q.args.pe = pe_updates;
+    q.args.status = c->d_status;
+    q.args.trace_L = trace_L;
+    q.args.trace_R = trace_R;
+    q.args.trace_P = trace_P;
+    q.args.batch = batch;
+    q.args.max_iter = max_iter;
+    q.args.alpha = scale;
+    q.stop_mode = stop_mode;
+    q.freeze_mode = freeze_mode;
+    q.trace = trace;
+    q.stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    switch (c->m) {
+    case 1: e = polarbp::launch_m1(q); break;
+    case 2: e = polarbp::launch_m2(q); break;
+    case 3: e = polarbp::launch_m3(q); break;
+    case 4: e = polarbp::launch_m4(q); break;
+    case 5: e = polarbp::launch_m5(q); break;
+    case 6: e = polarbp::launch_m6(q); break;
+    case 7: e = polarbp::launch_m7(q); break;
+    case 8: e = polarbp::launch_m8(q); break;
+    case 9: e = polarbp::launch_m9(q); break;
+    case 10: e = polarbp::launch_m10(q); break;
+    case 11: e = polarbp::launch_m11(q); break;
+    default: e = polarbp::launch_m12(q); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    return POLARBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polarbp_code** out)
+{
+    if (!out) return fail(POLARBP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const int m = exact_log2(N);
+    if (m < 1 || N > 32768) return fail(POLARBP_ERR_ARG, "N must be a power of two in [2, 32768]");
+    if (K < 0 || K > N) return fail(POLARBP_ERR_ARG, "K must be in [0, N]");
+    polarbp_code* c = new (std::nothrow) polarbp_code;
+    if (!c) return fail(POLARBP_ERR_NOMEM, "out of host memory");
+    c->N = N;
+    c->K = K;
+    c->m = m;
+    if (frozen_mask) {
+        c->frozen.assign(frozen_mask, frozen_mask + N);
+        int nf = 0;
+        for (int i = 0; i < N; ++i) {
+            if (c->frozen[i] > 1) {
+                delete c;
+                return fail(POLARBP_ERR_ARG, "frozen_mask entries must be 0 or 1");
+            }
+            nf += c->frozen[i];
+        }
+        if (nf != N - K) {
+            delete c;
+            return fail(POLARBP_ERR_ARG, "frozen_mask popcount must equal N - K");
+        }
+    } else {
+        if (!(z0 > 0.0 && z0 < 1.0)) {
+            delete c;
+            return fail(POLARBP_ERR_ARG, "z0 must be in (0, 1)");
+        }
+        bec_frozen_set(N, m, K, z0, c->frozen);
+    }
+    const int nw = (N + 31) / 32;
+    std::vector<uint32_t> words(nw, 0u);
+    for (int i = 0; i < N; ++i)
+        if (c->frozen[i]) words[i >> 5] |= 1u << (i & 31);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_frozen, nw * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_frozen, words.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        int rc = (e == cudaErrorMemoryAllocation) ? fail(POLARBP_ERR_NOMEM, "device allocation failed")
+                                                  : cuda_fail(e, "construct");
+        if (c->d_frozen) cudaFree(c->d_frozen);
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return POLARBP_OK;
+}
+
+int polarbp_frozen_set(int N, int K, double z0, uint8_t* frozen_mask)
+{
+    const int m = exact_log2(N);
+    if (m < 1 || N > 32768) return fail(POLARBP_ERR_ARG, "N must be a power of two in [2, 32768]");
+    if (K < 0 || K > N) return fail(POLARBP_ERR_ARG, "K must be in [0, N]");
+    if (!(z0 > 0.0 && z0 < 1.0)) return fail(POLARBP_ERR_ARG, "z0 must be in (0, 1)");
+    if (!frozen_mask) return fail(POLARBP_ERR_ARG, "frozen_mask is NULL");
+    std::vector<uint8_t> f;
+    bec_frozen_set(N, m, K, z0, f);
+    std::memcpy(frozen_mask, f.data(), (size_t)N);
+    return POLARBP_OK;
+}
+
+void polarbp_destroy(polarbp_code* c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    if (c->d_frozen) cudaFree(c->d_frozen);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+}
+
+int polarbp_code_info(const polarbp_code* c, int* N, int* K, int* m)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (N) *N = c->N;
+    if (K) *K = c->K;
+    if (m) *m = c->m;
+    return POLARBP_OK;
+}
+
+int polarbp_get_frozen_mask(const polarbp_code* c, uint8_t* frozen_mask)
+{
+    if (!c || !frozen_mask) return fail(POLARBP_ERR_ARG, "NULL argument");
+    std::memcpy(frozen_mask, c->frozen.data(), (size_t)c->N);
+    return POLARBP_OK;
+}
+
+int polarbp_encode(const polarbp_code* c, const uint8_t* u, uint8_t* x, int batch, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (batch == 0) return POLARBP_OK;
+    if (!u || !x || u == x) return fail(POLARBP_ERR_ARG, "u and x must be distinct device pointers");
+    int rc = check_device(c);
+    if (rc != POLARBP_OK) return rc;
+    const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
+    encode_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(u, x, c->N, c->m);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "encode launch");
+    return POLARBP_OK;
+}
+
+int polarbp_decode(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale, int stop_mode,
+                   int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates, void* stream)
+{
+    return decode_impl(c, llr, batch, max_iter, scale, stop_mode, freeze_mode, u_hat, iterations, pe_updates,
+                       nullptr, nullptr, nullptr, false, stream);
+}
+
+int polarbp_decode_trace(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale,
+                         int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates,
+                         float* trace_L, float* trace_R, int32_t* trace_P, void* stream)
+{
+    return decode_impl(c, llr, batch, max_iter, scale, stop_mode, freeze_mode, u_hat, iterations, pe_updates,
+                       trace_L, trace_R, trace_P, true, stream);
+}
+
+size_t polarbp_decode_host_workspace(const polarbp_code* c, int batch)
+{
+    if (!c || batch < 0) return 0;
+    return host_layout(c->N, batch).total;
+}
+
+int polarbp_decode_host(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale,
+                        int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates,
+                        void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (batch == 0) return POLARBP_OK;
+    if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be host pointers");
+    const HostLayout h = host_layout(c->N, batch);
+    if (!workspace || workspace_bytes < h.total) return fail(POLARBP_ERR_ARG, "workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    float* d_llr = reinterpret_cast<float*>(ws + h.llr);
+    uint8_t* d_u = reinterpret_cast<uint8_t*>(ws + h.u_hat);
+    int32_t* d_it = reinterpret_cast<int32_t*>(ws + h.iters);
+    int64_t* d_pe = reinterpret_cast<int64_t*>(ws + h.pe);
+    const size_t nllr = (size_t)batch * c->N;
+    cudaError_t e = cudaMemcpyAsync(d_llr, llr, nllr * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "llr upload");
+    int rc = decode_impl(c, d_llr, batch, max_iter, scale, stop_mode, freeze_mode, d_u, d_it, d_pe, nullptr, nullptr,
+                         nullptr, false, stream);
+    if (rc != POLARBP_OK) return rc;
+    e = cudaMemcpyAsync(u_hat, d_u, nllr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && iterations)
+        e = cudaMemcpyAsync(iterations, d_it, (size_t)batch * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && pe_updates)
+        e = cudaMemcpyAsync(pe_updates, d_pe, (size_t)batch * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "decode_host copies");
+    return POLARBP_OK;
+}
+
+int polarbp_awgn(const polarbp_code* c, uint64_t seed, uint64_t first_codeword, int batch, float ebn0_db, uint8_t* u,
+                 float* llr, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (c->K < 1) return fail(POLARBP_ERR_ARG, "the channel needs K >= 1 (rate > 0)");
+    if (!std::isfinite(ebn0_db)) return fail(POLARBP_ERR_ARG, "ebn0_db must be finite");
+    if (batch == 0) return POLARBP_OK;
+    if (!llr) return fail(POLARBP_ERR_ARG, "llr must be a device pointer");
+    int rc = check_device(c);
+    if (rc != POLARBP_OK) return rc;
+    const double rate = (double)c->K / (double)c->N;
+    const float sigma = (float)std::sqrt(1.0 / (2.0 * rate * std::pow(10.0, ebn0_db / 10.0)));
+    const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
+    awgn_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(c->d_frozen, c->N, c->m, seed,
+                                                                             first_codeword, sigma, u, llr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "awgn launch");
+    return POLARBP_OK;
+}
+
+int polarbp_get_status(const polarbp_code* c, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof h, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "get_status");
+    if (h & 1u) return fail(POLARBP_ERR_NONFINITE, "a decode saw a non-finite channel LLR");
+    return POLARBP_OK;
+}
+
+const char* polarbp_last_error(void) { return g_last_error.c_str(); }
+
+const char* polarbp_version(void) { return "polarbp 0.1 (sm_103a)"; }
+
+}  // extern "C"
