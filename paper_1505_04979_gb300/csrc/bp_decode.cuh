@@ -62,6 +62,18 @@ struct Geo {
         return r;
     }
     static constexpr int NR = M - NB;  // register columns
+    // Shared-memory layout of the buffers at the boundary between phases b and
+    // b+1: entry i sits at i + (i >> padsh(b)).  The shift minimises bank
+    // conflicts of the two phases' access patterns (found by enumerating them);
+    // with any shift the address of element e of a thread is a per-thread base
+    // plus a compile-time offset, so no address arithmetic is spent per access.
+    __host__ __device__ static constexpr int padsh(int b)
+    {
+        return M <= 7 ? 2 : (M <= 9 ? 3 : (b == 0 ? 5 : 3));
+    }
+    static constexpr int BUF = N + (N >> (M <= 7 ? 2 : 3)) + 4;  // floats per padded buffer
+    static constexpr int HDS = N < 32 ? 32 : N;                   // bytes per hard-decision row
+    static constexpr int RW = NW < 32 ? 1 : NW / 32;              // words per lane of an N-bit vector
     __host__ __device__ static constexpr int owner(int c) { return (c / 3) < (NP - 1) ? (c / 3) : (NP - 1); }
 };
 
@@ -75,8 +87,24 @@ __device__ __forceinline__ int elem_index(int t, int e)
     return (t & ((1 << lo) - 1)) | (e << lo) | ((t >> lo) << (lo + RB));
 }
 
-// XOR swizzle of float arrays in shared memory (stays inside each 32-entry row).
-__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 31); }
+template <int SH>
+__host__ __device__ __forceinline__ constexpr int padded(int i) { return i + (i >> SH); }
+
+// Padded address of element e of thread t in phase PH's mapping, for a buffer
+// with pad shift SH: the thread part and the element part add up.
+template <int M, int PH, int SH>
+__device__ __forceinline__ int padded_base(int t)
+{
+    constexpr int lo = Geo<M>::lo(PH);
+    constexpr int RB = Geo<M>::RB;
+    const int b = (t & ((1 << lo) - 1)) | ((t >> lo) << (lo + RB));
+    return b + (b >> SH);
+}
+template <int M, int PH, int SH>
+__host__ __device__ __forceinline__ constexpr int padded_off(int e)
+{
+    return (e << Geo<M>::lo(PH)) + ((e << Geo<M>::lo(PH)) >> SH);
+}
 
 // alpha * sign(x) sign(y) min(|x|, |y|)  (Eq. (1)).  The magnitude is exact,
 // the product by alpha rounds once; the sign bit is xor-ed in.
@@ -109,14 +137,14 @@ struct SmemLayout {
     using G = Geo<M>;
     static constexpr int N = G::N, NW = G::NW;
     static constexpr size_t off_Lb = 0;
-    static constexpr size_t off_Rx = off_Lb + sizeof(float) * G::NB * N;
-    static constexpr size_t off_U = off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * N;
+    static constexpr size_t off_Rx = off_Lb + sizeof(float) * G::NB * G::BUF;
+    static constexpr size_t off_U = (off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * G::BUF + 15) / 16 * 16;
     static constexpr size_t off_Fz = off_U + sizeof(uint32_t) * NW;
     static constexpr size_t off_Xf = off_Fz + sizeof(uint32_t) * NW;
     static constexpr size_t off_Ctl = (off_Xf + sizeof(uint32_t) * (M + 1) * NW + 15) / 16 * 16;
     static constexpr int CTL_INTS = CTL_EV + 2 * (M + 1);
     static constexpr size_t off_Hd = (off_Ctl + sizeof(int) * CTL_INTS + 15) / 16 * 16;
-    static constexpr size_t hd_bytes = (size_t)(M + 1) * N;
+    static constexpr size_t hd_bytes = (size_t)(M + 1) * G::HDS;
     static constexpr size_t bytes = (off_Hd + hd_bytes + 15) / 16 * 16;
 };
 
@@ -128,7 +156,7 @@ struct Smem {
     uint32_t* Fz;   // frozen mask
     uint32_t* Xf;   // [(M+1)][NW] hard decisions of the latest feedback event per column
     int* ctl;
-    uint8_t* hd;    // [(M+1)][N] hard-decision snapshots (0/1 bytes)
+    uint8_t* hd;    // [(M+1)][HDS] hard-decision snapshots (0/1 bytes)
     __device__ __forceinline__ explicit Smem(unsigned char* base)
     {
         using L = SmemLayout<M>;
@@ -148,17 +176,15 @@ struct Smem {
 __device__ __forceinline__ uint32_t bit_of(const uint32_t* words, int i) { return (words[i >> 5] >> (i & 31)) & 1u; }
 
 // ---------------------------------------------------------------------------
-// warp-level bit-vector helpers for the checks (word w = 32 r + lane)
+// warp-level bit-vector helpers for the checks
+// A CSFG of S positions (S a power of two) is held by the checker warp as
+// packed words: word w = 32 r + lane when S >= 32, else bits [0, S) of v[0] in
+// every lane.  Sizes are run-time values so the checker's code stays small.
 // ---------------------------------------------------------------------------
-template <int S>
-struct BlockBits {
-    static constexpr int W = S >= 32 ? S / 32 : 1;
-    static constexpr int R = (W + 31) / 32;
-};
-
 // four 0/1 bytes of a word -> 4 bits (byte k -> bit k)
 __device__ __forceinline__ uint32_t nib4(uint32_t w) { return (w * 0x01020408u) >> 24; }
 
+// 32 aligned 0/1 bytes -> one word (byte k -> bit k)
 __device__ __forceinline__ uint32_t pack32(const uint8_t* p32)
 {
     const uint4 a = reinterpret_cast<const uint4*>(p32)[0];
@@ -167,89 +193,88 @@ __device__ __forceinline__ uint32_t pack32(const uint8_t* p32)
            (nib4(b.y) << 20) | (nib4(b.z) << 24) | (nib4(b.w) << 28);
 }
 
-// S hard-decision bytes at hd[base..base+S) -> packed words
-template <int S>
-__device__ __forceinline__ void hd_load(const uint8_t* hd, int base, uint32_t (&v)[BlockBits<S>::R], int lane)
-{
-    if constexpr (S >= 32) {
-#pragma unroll
-        for (int r = 0; r < BlockBits<S>::R; ++r) {
-            const int w = 32 * r + lane;
-            v[r] = (w < BlockBits<S>::W) ? pack32(hd + base + 32 * w) : 0u;
-        }
-    } else {
-        const bool b = (lane < S) ? (hd[base + lane] != 0) : false;
-        v[0] = __ballot_sync(kFull, b);
-    }
-}
-
-template <int S>
-__device__ __forceinline__ void packed_load(const uint32_t* words, int base, uint32_t (&v)[BlockBits<S>::R],
-                                            int lane)
-{
-    if constexpr (S >= 32) {
-#pragma unroll
-        for (int r = 0; r < BlockBits<S>::R; ++r) {
-            const int w = 32 * r + lane;
-            v[r] = (w < BlockBits<S>::W) ? words[(base >> 5) + w] : 0u;
-        }
-    } else {
-        v[0] = (words[base >> 5] >> (base & 31)) & ((1u << S) - 1u);
-    }
-}
-
-template <int S>
-__device__ __forceinline__ void packed_store(uint32_t* words, int base, const uint32_t (&v)[BlockBits<S>::R],
-                                             int lane)
-{
-    if constexpr (S >= 32) {
-#pragma unroll
-        for (int r = 0; r < BlockBits<S>::R; ++r) {
-            const int w = 32 * r + lane;
-            if (w < BlockBits<S>::W) words[(base >> 5) + w] = v[r];
-        }
-    } else {
-        if (lane == 0) {
-            const uint32_t mask = ((1u << S) - 1u) << (base & 31);
-            uint32_t* p = words + (base >> 5);
-            *p = (*p & ~mask) | ((v[0] << (base & 31)) & mask);
-        }
-    }
-}
-
 __device__ __forceinline__ uint32_t xmask(int h)
 {
     return h == 1 ? 0x55555555u : h == 2 ? 0x33333333u : h == 4 ? 0x0F0F0F0Fu : h == 8 ? 0x00FF00FFu : 0x0000FFFFu;
 }
 
+__device__ __forceinline__ uint32_t low_mask(int S) { return S >= 32 ? 0xffffffffu : ((1u << S) - 1u); }
+
+// hard-decision bytes hd[base .. base+S) (rows of >= 32 bytes, 32-byte aligned)
+template <int RW>
+__device__ __forceinline__ void hd_load(const uint8_t* hd, int base, int S, uint32_t (&v)[RW], int lane)
+{
+    if (S >= 32) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int w = 32 * r + lane;
+            v[r] = (w < (S >> 5)) ? pack32(hd + base + 32 * w) : 0u;
+        }
+    } else {
+        v[0] = (pack32(hd + (base & ~31)) >> (base & 31)) & low_mask(S);
+#pragma unroll
+        for (int r = 1; r < RW; ++r) v[r] = 0u;
+    }
+}
+
+template <int RW>
+__device__ __forceinline__ void packed_load(const uint32_t* words, int base, int S, uint32_t (&v)[RW], int lane)
+{
+    if (S >= 32) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int w = 32 * r + lane;
+            v[r] = (w < (S >> 5)) ? words[(base >> 5) + w] : 0u;
+        }
+    } else {
+        v[0] = (words[base >> 5] >> (base & 31)) & low_mask(S);
+#pragma unroll
+        for (int r = 1; r < RW; ++r) v[r] = 0u;
+    }
+}
+
+template <int RW>
+__device__ __forceinline__ void packed_store(uint32_t* words, int base, int S, const uint32_t (&v)[RW], int lane)
+{
+    if (S >= 32) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int w = 32 * r + lane;
+            if (w < (S >> 5)) words[(base >> 5) + w] = v[r];
+        }
+    } else if (lane == 0) {
+        const uint32_t mask = low_mask(S) << (base & 31);
+        uint32_t* p = words + (base >> 5);
+        *p = (*p & ~mask) | ((v[0] << (base & 31)) & mask);
+    }
+}
+
 // v <- v . F^{(x) log2 S}: for every bit h of the position, entries with bit h
 // clear absorb (xor) the entry with bit h set.
-template <int S>
-__device__ __forceinline__ void polar_xform(uint32_t (&v)[BlockBits<S>::R], int lane)
+template <int RW>
+__device__ __forceinline__ void polar_xform(uint32_t (&v)[RW], int S, int lane)
 {
-    constexpr int R = BlockBits<S>::R;
-    constexpr int INW = S < 32 ? S : 32;
-#pragma unroll
-    for (int h = 1; h < INW; h <<= 1) {
+    const int inw = S < 32 ? S : 32;
+#pragma unroll 1
+    for (int h = 1; h < inw; h <<= 1) {
         const uint32_t mk = xmask(h);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] ^= (v[r] >> h) & mk;
+        for (int r = 0; r < RW; ++r) v[r] ^= (v[r] >> h) & mk;
     }
-    if constexpr (S > 32) {
-        constexpr int W = BlockBits<S>::W;
+    const int W = S >> 5;
+#pragma unroll 1
+    for (int d = 1; d < W; d <<= 1) {
+        if (d < 32) {
 #pragma unroll
-        for (int d = 1; d < W; d <<= 1) {
-            if (d < 32) {
+            for (int r = 0; r < RW; ++r) {
+                const uint32_t y = __shfl_xor_sync(kFull, v[r], d);
+                if (!(lane & d)) v[r] ^= y;
+            }
+        } else {
+            const int dr = d >> 5;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t y = __shfl_down_sync(kFull, v[r], d);
-                    if ((lane & d) == 0) v[r] ^= y;
-                }
-            } else {
-                const int dr = d / 32;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if ((r & dr) == 0) v[r] ^= v[r + dr];
+            for (int r = 0; r < RW; ++r) {
+                if (!(r & dr) && r + dr < RW) v[r] ^= v[r + dr];
             }
         }
     }
@@ -258,70 +283,193 @@ __device__ __forceinline__ void polar_xform(uint32_t (&v)[BlockBits<S>::R], int 
 // ---------------------------------------------------------------------------
 // checker warp
 // ---------------------------------------------------------------------------
-// After a freeze that ended at P, freeze every enclosing CSFG that has become
-// fully covered: its hard decision is its stored source bits re-encoded.
-template <int M, int JP>
-__device__ __forceinline__ void propagate(Smem<M>& sm, int P, int lane)
+template <int M>
+__device__ __forceinline__ void note_event(Smem<M>& sm, int J, int lo, int hi, int lane)
 {
-    if constexpr (JP >= 1) {
-        constexpr int Sp = Geo<M>::N >> JP;
-        constexpr int NW = Geo<M>::NW;
-        if ((P & (Sp - 1)) == 0) {
-            const int bp = P - Sp;
-            uint32_t v[BlockBits<Sp>::R];
-            packed_load<Sp>(sm.U, bp, v, lane);
-            polar_xform<Sp>(v, lane);
-            packed_store<Sp>(sm.Xf + JP * NW, bp, v, lane);
-            if (lane == 0) {
-                sm.ev_lo()[JP] = bp;
-                sm.ev_hi()[JP] = P;
-                sm.ctl[CTL_EVENT] = 1;
+    if (lane == 0) {
+        sm.ev_lo()[J] = lo;
+        sm.ev_hi()[J] = hi;
+        sm.ctl[CTL_EVENT] |= 1 << J;
+    }
+}
+
+// After a freeze that ended at P on stage J, freeze every enclosing CSFG that
+// has become fully covered: its hard decision is its stored source bits
+// re-encoded (the +-inf messages its own PEs would emit).
+template <int M>
+__device__ __forceinline__ void propagate(Smem<M>& sm, int P, int J, int lane)
+{
+    constexpr int N = Geo<M>::N, NW = Geo<M>::NW, RW = Geo<M>::RW;
+#pragma unroll 1
+    for (int jp = J - 1; jp >= 1; --jp) {
+        const int Sp = N >> jp;
+        if (P & (Sp - 1)) break;
+        const int bp = P - Sp;
+        uint32_t v[RW];
+        packed_load<RW>(sm.U, bp, Sp, v, lane);
+        polar_xform<RW>(v, Sp, lane);
+        packed_store<RW>(sm.Xf + jp * NW, bp, Sp, v, lane);
+        note_event(sm, jp, bp, P, lane);
+        __syncwarp();
+    }
+}
+
+// Speculative check of every stage's frontier CSFG under the covered prefix P0
+// of the start of the iteration, all stages at once.  CSFGs of >= 32 positions
+// are laid out word by word over the warp's lanes (stage j's words in an aligned
+// group of 2^(M-5-j) slots), so one sequence of shifts and lane shuffles applies
+// Eq. (3) to all of them; every smaller CSFG is handled whole by one lane.  The
+// result stays valid for stage j unless a shallower stage froze earlier in the
+// same iteration (the frontier then moved); resolve() re-checks those.
+template <int M>
+struct Spec {
+    static constexpr int N = 1 << M;
+    static constexpr int TW = N >= 64 ? N / 32 - 1 : 0;  // words of all CSFGs with >= 32 positions
+    static constexpr int R = TW > 0 ? (TW + 31) / 32 : 1;
+    static constexpr int JB = M - 5;                    // stages 1..JB have CSFGs of >= 32 positions
+    static constexpr int JS0 = JB >= 1 ? JB + 1 : 1;    // first stage with smaller CSFGs
+    static constexpr int NS = M - JS0 + 1;              // number of such stages (<= 5)
+    uint32_t x[R], u[R];  // Eq. (2) decisions and Eq. (3) source words of this lane's slots
+    int lvl[R], w[R];     // stage (0 = unused slot) and word-in-CSFG of each slot
+    uint32_t xs, us;      // the small CSFG this lane holds (lane < NS)
+    int fail;             // bit j: the speculative check of stage j fails Eq. (4)
+};
+
+template <int M>
+__device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int lane)
+{
+    using SP = Spec<M>;
+    constexpr int N = 1 << M;
+    constexpr int HDS = Geo<M>::HDS;
+    unsigned bad_levels = 0;
+    if constexpr (SP::TW > 0) {
+#pragma unroll
+        for (int r = 0; r < SP::R; ++r) {
+            const int sl = 32 * r + lane;
+            sp.lvl[r] = 0;
+            sp.w[r] = 0;
+            sp.x[r] = 0u;
+            if (sl < SP::TW) {
+                const int lw = 31 - __clz(N / 32 - sl - 1);  // log2 of the stage's word count
+                const int j = M - 5 - lw;
+                const int wi = sl - (N / 32 - (2 << lw));
+                const int base = (P0 >> (M - j)) << (M - j);
+                sp.lvl[r] = j;
+                sp.w[r] = wi;
+                sp.x[r] = pack32(sm.hd + j * HDS + base + 32 * wi);
             }
-            __syncwarp();
-            propagate<M, JP - 1>(sm, P, lane);
+            uint32_t v = sp.x[r];
+#pragma unroll
+            for (int h = 1; h < 32; h <<= 1) v ^= (v >> h) & xmask(h);
+            sp.u[r] = v;
+        }
+#pragma unroll
+        for (int d = 1; d < N / 64; d <<= 1) {
+            if (d < 32) {
+#pragma unroll
+                for (int r = 0; r < SP::R; ++r) {
+                    const uint32_t y = __shfl_xor_sync(kFull, sp.u[r], d);
+                    const int W = sp.lvl[r] ? (N >> (sp.lvl[r] + 5)) : 0;
+                    if (W > d && !(sp.w[r] & d)) sp.u[r] ^= y;
+                }
+            } else {
+                const int dr = d / 32;
+#pragma unroll
+                for (int r = 0; r < SP::R; ++r) {
+                    if ((r & dr) || r + dr >= SP::R) continue;
+                    const int W = sp.lvl[r] ? (N >> (sp.lvl[r] + 5)) : 0;
+                    if (W > d && !(sp.w[r] & d)) sp.u[r] ^= sp.u[r + dr];
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < SP::R; ++r) {
+            unsigned flag = 0;
+            if (sp.lvl[r]) {
+                const int j = sp.lvl[r];
+                const int base = (P0 >> (M - j)) << (M - j);
+                if (sp.u[r] & sm.Fz[(base >> 5) + sp.w[r]]) flag = 1u << j;
+            }
+            bad_levels |= __reduce_or_sync(kFull, flag);
         }
     }
-}
-
-// Eqs. (2)-(4) on the first uncovered CSFG of stage J.
-template <int M, int J>
-__device__ __forceinline__ void check_level(Smem<M>& sm, int& P, int lane)
-{
-    constexpr int N = Geo<M>::N;
-    constexpr int S = N >> J;
-    constexpr int R = BlockBits<S>::R;
-    constexpr int NW = Geo<M>::NW;
-    if (P >= N) return;
-    const int base = (P >> (M - J)) << (M - J);
-    uint32_t x[R], u[R], f[R];
-    hd_load<S>(sm.hd + J * N, base, x, lane);  // Eq. (2)
-#pragma unroll
-    for (int r = 0; r < R; ++r) u[r] = x[r];
-    polar_xform<S>(u, lane);                    // Eq. (3)
-    packed_load<S>(sm.Fz, base, f, lane);
-    bool bad = false;
-#pragma unroll
-    for (int r = 0; r < R; ++r) bad |= (u[r] & f[r]) != 0u;
-    if (__any_sync(kFull, bad)) return;         // Eq. (4) fails
-    packed_store<S>(sm.U, base, u, lane);
-    packed_store<S>(sm.Xf + J * NW, base, x, lane);
-    if (lane == 0) {
-        sm.ev_lo()[J] = base;
-        sm.ev_hi()[J] = base + S;
-        sm.ctl[CTL_EVENT] = 1;
+    {
+        unsigned flag = 0;
+        sp.xs = sp.us = 0u;
+        if (lane < SP::NS) {
+            const int j = SP::JS0 + lane;
+            const int S = N >> j;
+            const int base = (P0 >> (M - j)) << (M - j);
+            const uint32_t mk = low_mask(S);
+            const uint32_t xv = (pack32(sm.hd + j * HDS + (base & ~31)) >> (base & 31)) & mk;
+            uint32_t v = xv;
+            for (int h = 1; h < S; h <<= 1) v ^= (v >> h) & xmask(h);
+            sp.xs = xv;
+            sp.us = v;
+            if (v & (sm.Fz[base >> 5] >> (base & 31)) & mk) flag = 1u << j;
+        }
+        bad_levels |= __reduce_or_sync(kFull, flag);
     }
-    P = base + S;
-    __syncwarp();
-    propagate<M, J - 1>(sm, P, lane);
+    sp.fail = (int)bad_levels;
 }
 
-template <int M, int J>
-__device__ __forceinline__ void check_all(Smem<M>& sm, int& P, int& pe_it, int lane)
+// Stages 1..M in order (the checks depend on each other through P): commit the
+// speculative result when the frontier has not moved, else check the new
+// frontier CSFG with Eqs. (2)-(4).
+template <int M>
+__device__ __forceinline__ void resolve(Smem<M>& sm, Spec<M>& sp, int P0, int& P, int& pe_it, int lane)
 {
-    if constexpr (J <= M) {
-        check_level<M, J>(sm, P, lane);
-        if constexpr (J < M) pe_it += (Geo<M>::N - ((P >> (M - J)) << (M - J))) >> 1;
-        check_all<M, J + 1>(sm, P, pe_it, lane);
+    using SP = Spec<M>;
+    constexpr int N = Geo<M>::N, NW = Geo<M>::NW, RW = Geo<M>::RW, HDS = Geo<M>::HDS;
+#pragma unroll 1
+    for (int J = 1; J <= M; ++J) {
+        if (P < N) {
+            const int S = N >> J;
+            const int cand = (P >> (M - J)) << (M - J);
+            bool pass;
+            if (cand == ((P0 >> (M - J)) << (M - J))) {
+                pass = !((sp.fail >> J) & 1);
+                if (pass) {
+                    if (J <= SP::JB) {
+#pragma unroll
+                        for (int r = 0; r < SP::R; ++r) {
+                            if (sp.lvl[r] == J) {
+                                sm.U[(cand >> 5) + sp.w[r]] = sp.u[r];
+                                sm.Xf[J * NW + (cand >> 5) + sp.w[r]] = sp.x[r];
+                            }
+                        }
+                    } else if (lane == J - SP::JS0) {
+                        const uint32_t mk = low_mask(S) << (cand & 31);
+                        uint32_t* pu = sm.U + (cand >> 5);
+                        uint32_t* px = sm.Xf + J * NW + (cand >> 5);
+                        *pu = (*pu & ~mk) | ((sp.us << (cand & 31)) & mk);
+                        *px = (*px & ~mk) | ((sp.xs << (cand & 31)) & mk);
+                    }
+                }
+            } else {
+                uint32_t x[RW], u[RW], f[RW];
+                hd_load<RW>(sm.hd + J * HDS, cand, S, x, lane);  // Eq. (2)
+#pragma unroll
+                for (int r = 0; r < RW; ++r) u[r] = x[r];
+                polar_xform<RW>(u, S, lane);                    // Eq. (3)
+                packed_load<RW>(sm.Fz, cand, S, f, lane);
+                bool bad = false;
+#pragma unroll
+                for (int r = 0; r < RW; ++r) bad |= (u[r] & f[r]) != 0u;
+                pass = !__any_sync(kFull, bad);                 // Eq. (4)
+                if (pass) {
+                    packed_store<RW>(sm.U, cand, S, u, lane);
+                    packed_store<RW>(sm.Xf + J * NW, cand, S, x, lane);
+                }
+            }
+            if (pass) {
+                note_event(sm, J, cand, cand + S, lane);
+                P = cand + S;
+                __syncwarp();
+                propagate<M>(sm, P, J, lane);
+            }
+        }
+        if (J < M) pe_it += (N - ((P >> (M - J)) << (M - J))) >> 1;
     }
 }
 
@@ -329,14 +477,12 @@ __device__ __forceinline__ void check_all(Smem<M>& sm, int& P, int& pe_it, int l
 template <int M>
 __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
 {
-    constexpr int N = Geo<M>::N;
-    constexpr int R = BlockBits<N>::R;
-    constexpr int NW = Geo<M>::NW;
-    uint32_t u[R], x[R];
-    hd_load<N>(sm.hd + M * N, 0, u, lane);
-    hd_load<N>(sm.hd, 0, x, lane);
+    constexpr int N = Geo<M>::N, NW = Geo<M>::NW, RW = Geo<M>::RW, HDS = Geo<M>::HDS;
+    uint32_t u[RW], x[RW];
+    hd_load<RW>(sm.hd + M * HDS, 0, N, u, lane);
+    hd_load<RW>(sm.hd, 0, N, x, lane);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < RW; ++r) {
         const int w = (N >= 32) ? 32 * r + lane : 0;
         uint32_t cov;
         if (P >= 32 * (w + 1)) cov = kFull;
@@ -346,16 +492,16 @@ __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
         const uint32_t fz = (w < NW) ? sm.Fz[w] : 0u;
         u[r] = (us & cov) | (u[r] & ~fz & ~cov);
     }
-    polar_xform<N>(u, lane);
+    polar_xform<RW>(u, N, lane);
     bool same = true;
-    constexpr uint32_t valid = (N >= 32) ? kFull : ((1u << (N & 31)) - 1u);
+    const uint32_t valid = low_mask(N);
 #pragma unroll
-    for (int r = 0; r < R; ++r) same &= ((u[r] ^ x[r]) & valid) == 0u;
+    for (int r = 0; r < RW; ++r) same &= ((u[r] ^ x[r]) & valid) == 0u;
     return __all_sync(kFull, same);
 }
 
 template <int M, bool GSTOP, bool FREEZE>
-__device__ __noinline__ void checker(unsigned char* smem_base, int lane)
+__device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
 {
     constexpr int N = Geo<M>::N;
     Smem<M> sm(smem_base);
@@ -368,7 +514,10 @@ __device__ __noinline__ void checker(unsigned char* smem_base, int lane)
     int P = sm.ctl[CTL_P];
     int pe_it = N >> 1;  // stage 0 always runs
     if constexpr (FREEZE) {
-        check_all<M, 1>(sm, P, pe_it, lane);
+        Spec<M> sp;
+        const int P0 = P;
+        speculate<M>(sm, sp, P0, lane);
+        resolve<M>(sm, sp, P0, P, pe_it, lane);
     } else {
         pe_it = M * (N >> 1);
     }
@@ -394,22 +543,29 @@ struct Regs {
     float llr[Geo<M>::EL];
 };
 
-template <int M, int C>
-__device__ __forceinline__ float load_L(Regs<M>& rg, Smem<M>& sm, int e, int i)
+// L of column C at element e of the running phase PH.  Boundary column C is
+// the buffer of boundary C/3 - 1 (between phases C/3 - 1 and C/3).
+template <int M, int PH, int C>
+__device__ __forceinline__ float load_L(Regs<M>& rg, Smem<M>& sm, int e, int pb)
 {
     using G = Geo<M>;
-    if constexpr (G::is_boundary(C)) return sm.Lb[G::bslot(C) * G::N + swz(i)];
-    else return rg.Lr[G::rslot(C)][e];
+    if constexpr (G::is_boundary(C)) {
+        constexpr int SH = G::padsh(G::bslot(C));
+        return sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)];
+    } else {
+        return rg.Lr[G::rslot(C)][e];
+    }
 }
 
-template <int M, int C>
-__device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int i, float v)
+template <int M, int PH, int C>
+__device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb, float v)
 {
     using G = Geo<M>;
     if constexpr (C == 0) {
-        (void)rg; (void)sm; (void)e; (void)i; (void)v;
+        (void)rg; (void)sm; (void)e; (void)pb; (void)v;
     } else if constexpr (G::is_boundary(C)) {
-        sm.Lb[G::bslot(C) * G::N + swz(i)] = v;
+        constexpr int SH = G::padsh(G::bslot(C));
+        sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
     } else {
         rg.Lr[G::rslot(C)][e] = v;
     }
@@ -425,17 +581,22 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     constexpr int b = M - 1 - s;
     constexpr int k = b - G::lo(PH);
     constexpr bool snap = FREEZE || (GSTOP && s == M - 1);
-    const int thr = (s == 0) ? 0 : ((P0 >> (M - s)) << (M - s));
-    uint8_t* hd_next = sm.hd + (s + 1) * N;
+    const int thr = (s == 0 || !FREEZE) ? 0 : ((P0 >> (M - s)) << (M - s));
+    uint8_t* hd_next = sm.hd + (s + 1) * G::HDS;
+    // padded bases for the boundary columns read (s+1) and written (s) here
+    const int pb_in = G::is_boundary(s + 1) ? padded_base<M, PH, G::padsh(G::bslot(s + 1))>(tid) : 0;
+    const int pb_out = G::is_boundary(s) ? padded_base<M, PH, G::padsh(G::bslot(s))>(tid) : 0;
 #pragma unroll
     for (int e = 0; e < EL; ++e) {
         if (e & (1 << k)) continue;
         const int e2 = e | (1 << k);
         const int ia = elem_index<M, PH>(tid, e);
         const int ib = ia + (1 << b);
-        if (ia < thr) continue;  // PE inside a covered CSFG: skipped
-        const float La = load_L<M, s + 1>(rg, sm, e, ia);
-        const float Lb = load_L<M, s + 1>(rg, sm, e2, ib);
+        if constexpr (FREEZE && s > 0) {
+            if (ia < thr) continue;  // PE inside a covered CSFG: skipped
+        }
+        const float La = load_L<M, PH, s + 1>(rg, sm, e, pb_in);
+        const float Lb = load_L<M, PH, s + 1>(rg, sm, e2, pb_in);
         const float Ra = rg.R[e];
         const float Rb = rg.R[e2];
         const float t = __fadd_rn(Lb, Rb);
@@ -444,8 +605,8 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         const float nLb = __fadd_rn(Lb, g);
         const float nRa = fms(Ra, t, alpha);
         const float nRb = __fadd_rn(Rb, g);
-        store_L<M, s>(rg, sm, e, ia, nLa);
-        store_L<M, s>(rg, sm, e2, ib, nLb);
+        store_L<M, PH, s>(rg, sm, e, pb_out, nLa);
+        store_L<M, PH, s>(rg, sm, e2, pb_out, nLb);
         if constexpr (s == 0 && GSTOP) {
             sm.hd[ia] = __fadd_rn(Ra, nLa) < 0.f;
             sm.hd[ib] = __fadd_rn(Rb, nLb) < 0.f;
@@ -477,42 +638,51 @@ __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, boo
     constexpr int N = G::N, EL = G::EL;
     if constexpr (PH > 0) {
         if (worker) {
+            constexpr int SH = G::padsh(PH - 1);
+            const int pb = padded_base<M, PH, SH>(tid);
 #pragma unroll
-            for (int e = 0; e < EL; ++e) rg.R[e] = sm.Rx[((PH - 1) & 1) * N + swz(elem_index<M, PH>(tid, e))];
+            for (int e = 0; e < EL; ++e) rg.R[e] = sm.Rx[((PH - 1) & 1) * G::BUF + pb + padded_off<M, PH, SH>(e)];
         }
     }
     if (worker) run_stage<M, PH, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, P0, alpha, a, trace_base);
     if constexpr (PH + 1 < G::NP) {
         if (worker) {
+            constexpr int SH = G::padsh(PH);
+            const int pb = padded_base<M, PH, SH>(tid);
 #pragma unroll
-            for (int e = 0; e < EL; ++e) sm.Rx[(PH & 1) * N + swz(elem_index<M, PH>(tid, e))] = rg.R[e];
+            for (int e = 0; e < EL; ++e) sm.Rx[(PH & 1) * G::BUF + pb + padded_off<M, PH, SH>(e)] = rg.R[e];
         }
         __syncthreads();
         run_phase<M, PH + 1, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
     }
 }
 
-// Fix L of the columns that received a freeze event to (-1)^x_hat * inf.
+// Fix L of the columns that received a freeze event to (-1)^x_hat * inf.  Every
+// thread rewrites only entries it reads itself in the next iteration: register
+// columns in their owner phase's mapping, shared-memory columns in the mapping of
+// the phase that reads them (stage C-1).  No barrier is needed.
 template <int M, int C>
-__device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, bool worker)
+__device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, int mask)
 {
     using G = Geo<M>;
     if constexpr (C <= M) {
-        const int lo = sm.ev_lo()[C], hi = sm.ev_hi()[C];
-        if (hi > lo) {
+        if (mask & (1 << C)) {
+            const int lo = sm.ev_lo()[C], hi = sm.ev_hi()[C];
             const uint32_t* xf = sm.Xf + C * G::NW;
-            if constexpr (G::is_boundary(C)) {
-                for (int i = lo + tid; i < hi; i += blockDim.x)
-                    sm.Lb[G::bslot(C) * G::N + swz(i)] = bit_of(xf, i) ? -INFINITY : INFINITY;
-            } else if (worker) {
+            constexpr int PH = G::is_boundary(C) ? (C - 1) / 3 : G::owner(C);
+            constexpr int SH = G::is_boundary(C) ? G::padsh(G::bslot(C)) : 5;
+            const int pb = padded_base<M, PH, SH>(tid);
 #pragma unroll
-                for (int e = 0; e < G::EL; ++e) {
-                    const int i = elem_index<M, G::owner(C)>(tid, e);
-                    if (i >= lo && i < hi) rg.Lr[G::rslot(C)][e] = bit_of(xf, i) ? -INFINITY : INFINITY;
+            for (int e = 0; e < G::EL; ++e) {
+                const int i = elem_index<M, PH>(tid, e);
+                if (i >= lo && i < hi) {
+                    const float v = bit_of(xf, i) ? -INFINITY : INFINITY;
+                    if constexpr (G::is_boundary(C)) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
+                    else rg.Lr[G::rslot(C)][e] = v;
                 }
             }
         }
-        apply_events<M, C + 1>(rg, sm, tid, worker);
+        apply_events<M, C + 1>(rg, sm, tid, mask);
     }
 }
 
@@ -523,8 +693,9 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
     using G = Geo<M>;
     if constexpr (C <= M) {
         if constexpr (G::is_boundary(C)) {
+            constexpr int SH = G::padsh(G::bslot(C));
             for (int i = tid; i < G::N; i += blockDim.x)
-                a.trace_L[trace_base + (long long)C * G::N + i] = sm.Lb[G::bslot(C) * G::N + swz(i)];
+                a.trace_L[trace_base + (long long)C * G::N + i] = sm.Lb[G::bslot(C) * G::BUF + padded<SH>(i)];
         } else if (worker) {
 #pragma unroll
             for (int e = 0; e < G::EL; ++e)
@@ -551,7 +722,7 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
         sm.Fz[w] = a.frozen_words[w];
         sm.U[w] = 0u;
     }
-    for (int i = tid; i < G::NB * N; i += blockDim.x) sm.Lb[i] = 0.f;
+    for (int i = tid; i < G::NB * G::BUF; i += blockDim.x) sm.Lb[i] = 0.f;
     {
         uint32_t* hd32 = reinterpret_cast<uint32_t*>(sm.hd);
         for (int i = tid; i < (int)(SmemLayout<M>::hd_bytes / 4); i += blockDim.x) hd32[i] = 0u;
@@ -601,16 +772,18 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
         }
         run_phase<M, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
         __syncthreads();
-        if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane);
-        __syncthreads();
-        const bool done = sm.ctl[CTL_DONE] != 0;
-        if constexpr (FREEZE) {
-            if (sm.ctl[CTL_EVENT]) {
-                apply_events<M, 1>(rg, sm, tid, worker);
-                __syncthreads();
+        bool done = false;
+        if constexpr (GSTOP || FREEZE) {
+            if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane);
+            __syncthreads();
+            done = sm.ctl[CTL_DONE] != 0;
+            if constexpr (FREEZE) {
+                const int mask = sm.ctl[CTL_EVENT];
+                if (mask && worker) apply_events<M, 1>(rg, sm, tid, mask);
             }
         }
         if constexpr (TRACE) {
+            __syncthreads();
             trace_L_columns<M, 1>(rg, sm, tid, worker, a, trace_base);
             if (tid == 0) a.trace_P[cw * a.max_iter + (it - 1)] = sm.ctl[CTL_P];
         }
@@ -632,7 +805,7 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
     }
     if (tid == 0) {
         if (a.iters) a.iters[cw] = iters;
-        if (a.pe) a.pe[cw] = *sm.pe_acc();
+        if (a.pe) a.pe[cw] = (GSTOP || FREEZE) ? *sm.pe_acc() : (long long)iters * M * (N >> 1);
     }
 }
 
