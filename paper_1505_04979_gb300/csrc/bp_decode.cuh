@@ -72,7 +72,9 @@ struct Geo {
         return M <= 7 ? 2 : (M <= 9 ? 3 : (b == 0 ? 5 : 3));
     }
     static constexpr int BUF = N + (N >> (M <= 7 ? 2 : 3)) + 4;  // floats per padded buffer
-    static constexpr int HDS = N < 32 ? 32 : N;                   // bytes per hard-decision row
+    // hard-decision snapshots: one byte per worker thread per column (bit e =
+    // decision on the thread's element e), rows of >= 32 bytes, 32-byte aligned
+    static constexpr int HDS = T < 32 ? 32 : T;
     static constexpr int RW = NW < 32 ? 1 : NW / 32;              // words per lane of an N-bit vector
     __host__ __device__ static constexpr int owner(int c) { return (c / 3) < (NP - 1) ? (c / 3) : (NP - 1); }
 };
@@ -138,7 +140,8 @@ struct SmemLayout {
     static constexpr int N = G::N, NW = G::NW;
     static constexpr size_t off_Lb = 0;
     static constexpr size_t off_Rx = off_Lb + sizeof(float) * G::NB * G::BUF;
-    static constexpr size_t off_U = (off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * G::BUF + 15) / 16 * 16;
+    static constexpr size_t off_Llr = (off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * G::BUF + 15) / 16 * 16;
+    static constexpr size_t off_U = off_Llr + sizeof(float) * G::N;
     static constexpr size_t off_Fz = off_U + sizeof(uint32_t) * NW;
     static constexpr size_t off_Xf = off_Fz + sizeof(uint32_t) * NW;
     static constexpr size_t off_Ctl = (off_Xf + sizeof(uint32_t) * (M + 1) * NW + 15) / 16 * 16;
@@ -152,16 +155,18 @@ template <int M>
 struct Smem {
     float* Lb;
     float* Rx;
+    float* llr;     // channel LLRs, [EL][T] (element e of thread t at e * T + t)
     uint32_t* U;    // stored source bits of covered positions
     uint32_t* Fz;   // frozen mask
     uint32_t* Xf;   // [(M+1)][NW] hard decisions of the latest feedback event per column
     int* ctl;
-    uint8_t* hd;    // [(M+1)][HDS] hard-decision snapshots (0/1 bytes)
+    uint8_t* hd;    // [(M+1)][HDS] hard-decision snapshots (one byte per thread)
     __device__ __forceinline__ explicit Smem(unsigned char* base)
     {
         using L = SmemLayout<M>;
         Lb = reinterpret_cast<float*>(base + L::off_Lb);
         Rx = reinterpret_cast<float*>(base + L::off_Rx);
+        llr = reinterpret_cast<float*>(base + L::off_Llr);
         U = reinterpret_cast<uint32_t*>(base + L::off_U);
         Fz = reinterpret_cast<uint32_t*>(base + L::off_Fz);
         Xf = reinterpret_cast<uint32_t*>(base + L::off_Xf);
@@ -184,15 +189,6 @@ __device__ __forceinline__ uint32_t bit_of(const uint32_t* words, int i) { retur
 // four 0/1 bytes of a word -> 4 bits (byte k -> bit k)
 __device__ __forceinline__ uint32_t nib4(uint32_t w) { return (w * 0x01020408u) >> 24; }
 
-// 32 aligned 0/1 bytes -> one word (byte k -> bit k)
-__device__ __forceinline__ uint32_t pack32(const uint8_t* p32)
-{
-    const uint4 a = reinterpret_cast<const uint4*>(p32)[0];
-    const uint4 b = reinterpret_cast<const uint4*>(p32)[1];
-    return nib4(a.x) | (nib4(a.y) << 4) | (nib4(a.z) << 8) | (nib4(a.w) << 12) | (nib4(b.x) << 16) |
-           (nib4(b.y) << 20) | (nib4(b.z) << 24) | (nib4(b.w) << 28);
-}
-
 __device__ __forceinline__ uint32_t xmask(int h)
 {
     return h == 1 ? 0x55555555u : h == 2 ? 0x33333333u : h == 4 ? 0x0F0F0F0Fu : h == 8 ? 0x00FF00FFu : 0x0000FFFFu;
@@ -200,21 +196,66 @@ __device__ __forceinline__ uint32_t xmask(int h)
 
 __device__ __forceinline__ uint32_t low_mask(int S) { return S >= 32 ? 0xffffffffu : ((1u << S) - 1u); }
 
-// hard-decision bytes hd[base .. base+S) (rows of >= 32 bytes, 32-byte aligned)
-template <int RW>
-__device__ __forceinline__ void hd_load(const uint8_t* hd, int base, int S, uint32_t (&v)[RW], int lane)
+// bit e of each of four bytes -> 4 bits (byte k -> bit k)
+__device__ __forceinline__ uint32_t nib_bit(uint32_t v, int e) { return (((v >> e) & 0x01010101u) * 0x01020408u) >> 24; }
+
+// Decisions of positions [i0, i0 + 32) (i0 a multiple of 32), in natural
+// order, from a snapshot row written in a phase whose register bits start at
+// bit lo: byte t holds, in bit e, the decision on element e of thread t, i.e.
+// on position (t & (2^lo - 1)) | e << lo | (t >> lo) << (lo + 3).  The
+// positions of one word come from 32, 16, 8 or 4 consecutive bytes depending
+// on lo.
+__device__ __forceinline__ uint32_t hd_word(const uint8_t* row, int lo, int i0)
 {
-    if (S >= 32) {
-#pragma unroll
-        for (int r = 0; r < RW; ++r) {
-            const int w = 32 * r + lane;
-            v[r] = (w < (S >> 5)) ? pack32(hd + base + 32 * w) : 0u;
-        }
-    } else {
-        v[0] = (pack32(hd + (base & ~31)) >> (base & 31)) & low_mask(S);
-#pragma unroll
-        for (int r = 1; r < RW; ++r) v[r] = 0u;
+    if (lo == 0) return *reinterpret_cast<const uint32_t*>(row + (i0 >> 3));
+    if (lo >= 5) {
+        const int t0 = (i0 & ((1 << lo) - 1)) | ((i0 >> (lo + 3)) << lo);
+        const int e = (i0 >> lo) & 7;
+        const uint4 a = *reinterpret_cast<const uint4*>(row + t0);
+        const uint4 b = *reinterpret_cast<const uint4*>(row + t0 + 16);
+        return nib_bit(a.x, e) | (nib_bit(a.y, e) << 4) | (nib_bit(a.z, e) << 8) | (nib_bit(a.w, e) << 12) |
+               (nib_bit(b.x, e) << 16) | (nib_bit(b.y, e) << 20) | (nib_bit(b.z, e) << 24) | (nib_bit(b.w, e) << 28);
     }
+    if (lo == 4) {
+        const int t0 = (i0 >> 7) << 4;
+        const int e = (i0 >> 4) & 7;
+        const uint4 a = *reinterpret_cast<const uint4*>(row + t0);
+        const uint32_t l = nib_bit(a.x, e) | (nib_bit(a.y, e) << 4) | (nib_bit(a.z, e) << 8) | (nib_bit(a.w, e) << 12);
+        const uint32_t h = nib_bit(a.x, e + 1) | (nib_bit(a.y, e + 1) << 4) | (nib_bit(a.z, e + 1) << 8) |
+                           (nib_bit(a.w, e + 1) << 12);
+        return l | (h << 16);
+    }
+    if (lo == 3) {
+        const int t0 = (i0 >> 6) << 3;
+        const int e = (i0 >> 3) & 7;
+        const uint2 a = *reinterpret_cast<const uint2*>(row + t0);
+        uint32_t w = 0;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) w |= (nib_bit(a.x, e + d) | (nib_bit(a.y, e + d) << 4)) << (8 * d);
+        return w;
+    }
+    const uint32_t v = *reinterpret_cast<const uint32_t*>(row + ((i0 >> 5) << 2));
+    uint32_t w = 0;
+    if (lo == 2) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) w |= nib_bit(v, e) << (4 * e);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t n = nib_bit(v, e);
+            w |= ((n & 3u) << (2 * e)) | ((n >> 2) << (16 + 2 * e));
+        }
+    }
+    return w;
+}
+
+// register-bit base of the phase that writes the snapshot of column c
+// (column 0: stage 0's channel-side decisions; column c >= 1: R[c] after stage c-1)
+template <int M>
+__device__ __forceinline__ int snap_lo(int c)
+{
+    const int ph = c == 0 ? 0 : (c - 1) / 3;
+    return (ph == Geo<M>::NP - 1) ? 0 : (M - 3 - 3 * ph);
 }
 
 template <int RW>
@@ -336,13 +377,13 @@ struct Spec {
 };
 
 template <int M>
-__device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int lane)
+__device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int jmin, int lane)
 {
     using SP = Spec<M>;
     constexpr int N = 1 << M;
     constexpr int HDS = Geo<M>::HDS;
     unsigned bad_levels = 0;
-    if constexpr (SP::TW > 0) {
+    if constexpr (SP::TW > 0) if (jmin <= SP::JB) {
 #pragma unroll
         for (int r = 0; r < SP::R; ++r) {
             const int sl = 32 * r + lane;
@@ -356,7 +397,7 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
                 const int base = (P0 >> (M - j)) << (M - j);
                 sp.lvl[r] = j;
                 sp.w[r] = wi;
-                sp.x[r] = pack32(sm.hd + j * HDS + base + 32 * wi);
+                sp.x[r] = hd_word(sm.hd + j * HDS, snap_lo<M>(j), base + 32 * wi);
             }
             uint32_t v = sp.x[r];
 #pragma unroll
@@ -396,14 +437,15 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
     {
         unsigned flag = 0;
         sp.xs = sp.us = 0u;
-        if (lane < SP::NS) {
+        if (lane < SP::NS && SP::JS0 + lane >= jmin) {
             const int j = SP::JS0 + lane;
             const int S = N >> j;
             const int base = (P0 >> (M - j)) << (M - j);
             const uint32_t mk = low_mask(S);
-            const uint32_t xv = (pack32(sm.hd + j * HDS + (base & ~31)) >> (base & 31)) & mk;
+            const uint32_t xv = (hd_word(sm.hd + j * HDS, snap_lo<M>(j), base & ~31) >> (base & 31)) & mk;
             uint32_t v = xv;
-            for (int h = 1; h < S; h <<= 1) v ^= (v >> h) & xmask(h);
+#pragma unroll
+            for (int h = 1; h < 16; h <<= 1) v ^= (v >> h) & xmask(h);  // steps >= S act on zero bits
             sp.xs = xv;
             sp.us = v;
             if (v & (sm.Fz[base >> 5] >> (base & 31)) & mk) flag = 1u << j;
@@ -413,64 +455,55 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
     sp.fail = (int)bad_levels;
 }
 
-// Stages 1..M in order (the checks depend on each other through P): commit the
-// speculative result when the frontier has not moved, else check the new
-// frontier CSFG with Eqs. (2)-(4).
+// Stages 1..M in order (the checks depend on each other through P).  All
+// stages at or below jmin are checked speculatively against the current
+// frontier; the first stage that passes is committed (its CSFG frozen, P moved
+// to the CSFG's end, enclosing CSFGs completed), which moves the frontier of
+// every deeper stage, so those are checked again from there.  Stages before
+// the first pass failed against the frontier they would have seen.  Returns
+// the PE updates of the iteration (Sec. IV count; stage s runs the PEs outside
+// covered CSFGs given P after the check of stage s).
 template <int M>
-__device__ __forceinline__ void resolve(Smem<M>& sm, Spec<M>& sp, int P0, int& P, int& pe_it, int lane)
+__device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
 {
     using SP = Spec<M>;
-    constexpr int N = Geo<M>::N, NW = Geo<M>::NW, RW = Geo<M>::RW, HDS = Geo<M>::HDS;
+    constexpr int N = Geo<M>::N, NW = Geo<M>::NW;
+    int jmin = 1;
+    int Ps = P;  // lane s (1 <= s < M): P seen by stage s, i.e. after the last commit at a stage <= s
 #pragma unroll 1
-    for (int J = 1; J <= M; ++J) {
-        if (P < N) {
-            const int S = N >> J;
-            const int cand = (P >> (M - J)) << (M - J);
-            bool pass;
-            if (cand == ((P0 >> (M - J)) << (M - J))) {
-                pass = !((sp.fail >> J) & 1);
-                if (pass) {
-                    if (J <= SP::JB) {
+    while (P < N && jmin <= M) {
+        Spec<M> sp;
+        speculate<M>(sm, sp, P, jmin, lane);
+        const unsigned wanted = ((2u << M) - 1u) & ~((1u << jmin) - 1u);
+        const unsigned pass = ~(unsigned)sp.fail & wanted;
+        if (!pass) break;
+        const int J = __ffs(pass) - 1;
+        const int S = N >> J;
+        const int cand = (P >> (M - J)) << (M - J);
+        if (J <= SP::JB) {
 #pragma unroll
-                        for (int r = 0; r < SP::R; ++r) {
-                            if (sp.lvl[r] == J) {
-                                sm.U[(cand >> 5) + sp.w[r]] = sp.u[r];
-                                sm.Xf[J * NW + (cand >> 5) + sp.w[r]] = sp.x[r];
-                            }
-                        }
-                    } else if (lane == J - SP::JS0) {
-                        const uint32_t mk = low_mask(S) << (cand & 31);
-                        uint32_t* pu = sm.U + (cand >> 5);
-                        uint32_t* px = sm.Xf + J * NW + (cand >> 5);
-                        *pu = (*pu & ~mk) | ((sp.us << (cand & 31)) & mk);
-                        *px = (*px & ~mk) | ((sp.xs << (cand & 31)) & mk);
-                    }
-                }
-            } else {
-                uint32_t x[RW], u[RW], f[RW];
-                hd_load<RW>(sm.hd + J * HDS, cand, S, x, lane);  // Eq. (2)
-#pragma unroll
-                for (int r = 0; r < RW; ++r) u[r] = x[r];
-                polar_xform<RW>(u, S, lane);                    // Eq. (3)
-                packed_load<RW>(sm.Fz, cand, S, f, lane);
-                bool bad = false;
-#pragma unroll
-                for (int r = 0; r < RW; ++r) bad |= (u[r] & f[r]) != 0u;
-                pass = !__any_sync(kFull, bad);                 // Eq. (4)
-                if (pass) {
-                    packed_store<RW>(sm.U, cand, S, u, lane);
-                    packed_store<RW>(sm.Xf + J * NW, cand, S, x, lane);
+            for (int r = 0; r < SP::R; ++r) {
+                if (sp.lvl[r] == J) {
+                    sm.U[(cand >> 5) + sp.w[r]] = sp.u[r];
+                    sm.Xf[J * NW + (cand >> 5) + sp.w[r]] = sp.x[r];
                 }
             }
-            if (pass) {
-                note_event(sm, J, cand, cand + S, lane);
-                P = cand + S;
-                __syncwarp();
-                propagate<M>(sm, P, J, lane);
-            }
+        } else if (lane == J - SP::JS0) {
+            const uint32_t mk = low_mask(S) << (cand & 31);
+            uint32_t* pu = sm.U + (cand >> 5);
+            uint32_t* px = sm.Xf + J * NW + (cand >> 5);
+            *pu = (*pu & ~mk) | ((sp.us << (cand & 31)) & mk);
+            *px = (*px & ~mk) | ((sp.xs << (cand & 31)) & mk);
         }
-        if (J < M) pe_it += (N - ((P >> (M - J)) << (M - J))) >> 1;
+        note_event(sm, J, cand, cand + S, lane);
+        P = cand + S;
+        __syncwarp();
+        propagate<M>(sm, P, J, lane);
+        if (lane >= J) Ps = P;
+        jmin = J + 1;
     }
+    const int pe = (lane >= 1 && lane < M) ? (N - ((Ps >> (M - lane)) << (M - lane))) >> 1 : 0;
+    return (int)__reduce_add_sync(kFull, (unsigned)pe) + (N >> 1);
 }
 
 // G-matrix stop: u_hat . F^{(x)M} == HD(R[0] + L[0]).
@@ -479,8 +512,17 @@ __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
 {
     constexpr int N = Geo<M>::N, NW = Geo<M>::NW, RW = Geo<M>::RW, HDS = Geo<M>::HDS;
     uint32_t u[RW], x[RW];
-    hd_load<RW>(sm.hd + M * HDS, 0, N, u, lane);
-    hd_load<RW>(sm.hd, 0, N, x, lane);
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int w = 32 * r + lane;
+        const bool in = (N >= 32) ? (w < NW) : (lane == 0);
+        u[r] = in ? hd_word(sm.hd + M * HDS, 0, 32 * w) & low_mask(N) : 0u;
+        x[r] = in ? hd_word(sm.hd, snap_lo<M>(0), 32 * w) & low_mask(N) : 0u;
+        if (N < 32) {
+            u[r] = __shfl_sync(kFull, u[r], 0);
+            x[r] = __shfl_sync(kFull, x[r], 0);
+        }
+    }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
         const int w = (N >= 32) ? 32 * r + lane : 0;
@@ -514,10 +556,7 @@ __device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
     int P = sm.ctl[CTL_P];
     int pe_it = N >> 1;  // stage 0 always runs
     if constexpr (FREEZE) {
-        Spec<M> sp;
-        const int P0 = P;
-        speculate<M>(sm, sp, P0, lane);
-        resolve<M>(sm, sp, P0, P, pe_it, lane);
+        pe_it = resolve<M>(sm, P, lane);
     } else {
         pe_it = M * (N >> 1);
     }
@@ -540,7 +579,6 @@ template <int M>
 struct Regs {
     float R[Geo<M>::EL];
     float Lr[Geo<M>::NR][Geo<M>::EL];
-    float llr[Geo<M>::EL];
 };
 
 // L of column C at element e of the running phase PH.  Boundary column C is
@@ -557,17 +595,21 @@ __device__ __forceinline__ float load_L(Regs<M>& rg, Smem<M>& sm, int e, int pb)
     }
 }
 
+// Store L of column C; with keep set (the PE lies in a covered CSFG) the old
+// value, possibly a +-inf freeze feedback, stays.  Covered PEs are still
+// evaluated: their R outputs are never read again, and evaluating them keeps
+// the sweep free of branches.
 template <int M, int PH, int C>
-__device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb, float v)
+__device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb, float v, bool keep)
 {
     using G = Geo<M>;
     if constexpr (C == 0) {
-        (void)rg; (void)sm; (void)e; (void)pb; (void)v;
+        (void)rg; (void)sm; (void)e; (void)pb; (void)v; (void)keep;
     } else if constexpr (G::is_boundary(C)) {
         constexpr int SH = G::padsh(G::bslot(C));
-        sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
+        if (!keep) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
     } else {
-        rg.Lr[G::rslot(C)][e] = v;
+        rg.Lr[G::rslot(C)][e] = keep ? rg.Lr[G::rslot(C)][e] : v;
     }
 }
 
@@ -582,7 +624,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     constexpr int k = b - G::lo(PH);
     constexpr bool snap = FREEZE || (GSTOP && s == M - 1);
     const int thr = (s == 0 || !FREEZE) ? 0 : ((P0 >> (M - s)) << (M - s));
-    uint8_t* hd_next = sm.hd + (s + 1) * G::HDS;
+    uint32_t xbyte = 0;  // stage 0: decisions on R[0] + L[0] (G-matrix stop)
     // padded bases for the boundary columns read (s+1) and written (s) here
     const int pb_in = G::is_boundary(s + 1) ? padded_base<M, PH, G::padsh(G::bslot(s + 1))>(tid) : 0;
     const int pb_out = G::is_boundary(s) ? padded_base<M, PH, G::padsh(G::bslot(s))>(tid) : 0;
@@ -592,9 +634,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         const int e2 = e | (1 << k);
         const int ia = elem_index<M, PH>(tid, e);
         const int ib = ia + (1 << b);
-        if constexpr (FREEZE && s > 0) {
-            if (ia < thr) continue;  // PE inside a covered CSFG: skipped
-        }
+        const bool covered = FREEZE && s > 0 && ia < thr;  // PE inside a covered CSFG
         const float La = load_L<M, PH, s + 1>(rg, sm, e, pb_in);
         const float Lb = load_L<M, PH, s + 1>(rg, sm, e2, pb_in);
         const float Ra = rg.R[e];
@@ -605,11 +645,11 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         const float nLb = __fadd_rn(Lb, g);
         const float nRa = fms(Ra, t, alpha);
         const float nRb = __fadd_rn(Rb, g);
-        store_L<M, PH, s>(rg, sm, e, pb_out, nLa);
-        store_L<M, PH, s>(rg, sm, e2, pb_out, nLb);
+        store_L<M, PH, s>(rg, sm, e, pb_out, nLa, covered);
+        store_L<M, PH, s>(rg, sm, e2, pb_out, nLb, covered);
         if constexpr (s == 0 && GSTOP) {
-            sm.hd[ia] = __fadd_rn(Ra, nLa) < 0.f;
-            sm.hd[ib] = __fadd_rn(Rb, nLb) < 0.f;
+            xbyte |= (__fadd_rn(Ra, nLa) < 0.f ? 1u : 0u) << e;
+            xbyte |= (__fadd_rn(Rb, nLb) < 0.f ? 1u : 0u) << e2;
         }
         if constexpr (s == 0 && TRACE) {
             a.trace_L[trace_base + ia] = nLa;
@@ -617,10 +657,13 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         }
         rg.R[e] = nRa;
         rg.R[e2] = nRb;
-        if constexpr (snap) {
-            hd_next[ia] = nRa < 0.f;
-            hd_next[ib] = nRb < 0.f;
-        }
+    }
+    if constexpr (s == 0 && GSTOP) sm.hd[tid] = (uint8_t)xbyte;
+    if constexpr (snap) {
+        uint32_t byte = 0;
+#pragma unroll
+        for (int e = 0; e < EL; ++e) byte |= (rg.R[e] < 0.f ? 1u : 0u) << e;
+        sm.hd[(s + 1) * G::HDS + tid] = (uint8_t)byte;
     }
     if constexpr (TRACE) {
 #pragma unroll
@@ -742,8 +785,7 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
         for (int e = 0; e < EL; ++e) {
             const float v = a.llr[cw * N + elem_index<M, 0>(tid, e)];
             finite &= isfinite(v);
-            rg.llr[e] = v;
-            rg.R[e] = v;
+            sm.llr[e * T + tid] = v;
         }
         if (!finite) atomicOr(a.status, 1u);
 #pragma unroll
@@ -764,10 +806,10 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
         const long long trace_base = TRACE ? (cw * a.max_iter + (it - 1)) * (long long)(M + 1) * N : 0;
         if (worker) {
 #pragma unroll
-            for (int e = 0; e < EL; ++e) rg.R[e] = rg.llr[e];
+            for (int e = 0; e < EL; ++e) rg.R[e] = sm.llr[e * T + tid];
             if constexpr (TRACE) {
 #pragma unroll
-                for (int e = 0; e < EL; ++e) a.trace_R[trace_base + elem_index<M, 0>(tid, e)] = rg.llr[e];
+                for (int e = 0; e < EL; ++e) a.trace_R[trace_base + elem_index<M, 0>(tid, e)] = rg.R[e];
             }
         }
         run_phase<M, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
@@ -794,12 +836,20 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
     // output: stored bits on covered positions, HD(R[M]) elsewhere, 0 on frozen
     if (worker) {
         const int P = sm.ctl[CTL_P];
+        // HD(R[M]) of the last sweep: the snapshot byte when one is kept, else R itself
+        uint32_t hdM = 0;
+        if constexpr (GSTOP || FREEZE) {
+            hdM = sm.hd[M * G::HDS + tid];
+        } else {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) hdM |= (rg.R[e] < 0.f ? 1u : 0u) << e;
+        }
 #pragma unroll
         for (int e = 0; e < EL; ++e) {
             const int i = elem_index<M, G::NP - 1>(tid, e);
             uint8_t bit;
             if (i < P) bit = (uint8_t)bit_of(sm.U, i);
-            else bit = bit_of(sm.Fz, i) ? 0 : (rg.R[e] < 0.f ? 1 : 0);
+            else bit = bit_of(sm.Fz, i) ? 0 : (uint8_t)((hdM >> e) & 1u);
             a.u_hat[cw * N + i] = bit;
         }
     }
