@@ -183,6 +183,33 @@ int polarbp_awgn(const polarbp_code* code, uint64_t seed, uint64_t first_codewor
                  uint8_t* u, float* llr, void* stream);
 
 /*
+ * polarbp_decode_host_noalloc -- polarbp_decode_host without a caller-supplied
+ * workspace, for callers that may not allocate device memory: real-time
+ * receive chains that forbid cudaMalloc once running (it can synchronise the
+ * device and take milliseconds), and plug-ins whose host application owns all
+ * device memory.  The paper has no counterpart; this is a deployment variant.
+ *
+ * The staging buffers live in one fixed array of POLARBP_NOALLOC_SCRATCH_BYTES
+ * in device global memory, part of this library; every GPU that loads the
+ * library holds it until the process exits.  The call allocates nothing.
+ *   Arguments and results are those of polarbp_decode_host (host arrays).
+ *   batch must satisfy polarbp_decode_host_workspace(code, batch) <=
+ *   POLARBP_NOALLOC_SCRATCH_BYTES (about 3,200 codewords at N = 1024);
+ *   larger batches return POLARBP_ERR_ARG with the limit in the message.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and leave the
+ * last call's contents in it; nothing in it needs to start at zero (each call
+ * writes every byte it reads).  Calls that overlap on the GPU -- on different
+ * streams or host threads at the same time on the same device -- race on the
+ * array: serialise them.  Synchronises `stream` before returning.
+ */
+#define POLARBP_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int polarbp_decode_host_noalloc(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
+                                int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,
+                                int64_t* pe_updates, void* stream);
+
+/*
  * polarbp_get_status -- read and clear the handle's device status word.  Waits
  * for `stream`.  Returns POLARBP_ERR_NONFINITE when a decode since the last
  * call saw a non-finite LLR, else POLARBP_OK (or POLARBP_ERR_CUDA).

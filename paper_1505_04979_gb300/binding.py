@@ -53,6 +53,8 @@ _SIGS = {
     "polarbp_decode_host_workspace": (ctypes.c_size_t, [_VP, ctypes.c_int]),
     "polarbp_decode_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                            ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "polarbp_decode_host_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                                   ctypes.c_int, _VP, _VP, _VP, _VP]),
     "polarbp_awgn": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_float, _VP, _VP,
                                     _VP]),
     "polarbp_get_status": (ctypes.c_int, [_VP, _VP]),
@@ -223,6 +225,18 @@ def polarbp_decode_host(code: PolarCode, llr_host, max_iter: int, scale: float, 
     _check(lib().polarbp_decode_host(code.handle, _ptr(llr_host), B, max_iter, scale, stop_mode, freeze_mode,
                                      _ptr(u_hat_host), _ptr(iterations_host), _ptr(pe_host), _ptr(workspace),
                                      workspace.numel(), _stream(stream)), "polarbp_decode_host")
+
+
+def polarbp_decode_host_noalloc(code: PolarCode, llr_host, max_iter: int, scale: float, stop_mode: int,
+                                freeze_mode: int, u_hat_host, iterations_host, pe_host, stream=None) -> None:
+    """polarbp_decode_host staging through the library's built-in device array (no allocation)."""
+    B = llr_host.shape[0]
+    for t, name in ((llr_host, "llr"), (u_hat_host, "u_hat")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    _check(lib().polarbp_decode_host_noalloc(code.handle, _ptr(llr_host), B, max_iter, scale, stop_mode, freeze_mode,
+                                             _ptr(u_hat_host), _ptr(iterations_host), _ptr(pe_host),
+                                             _stream(stream)), "polarbp_decode_host_noalloc")
 
 
 def polarbp_get_status(code: PolarCode, stream=None) -> int:

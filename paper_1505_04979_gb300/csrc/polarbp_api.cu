@@ -3,6 +3,7 @@
 // dispatch of the decode kernels in bp_decode.cuh.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -258,6 +259,33 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     return POLARBP_OK;
 }
 
+// Staging area of polarbp_decode_host_noalloc: a fixed device array that is
+// part of the library image, so the entry point never allocates.  Host code
+// must not pass the symbol itself to a kernel or copy (on the host it names a
+// host-side stand-in); it uses the device address looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[POLARBP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch_address(void** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(POLARBP_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the built-in scratch");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return POLARBP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -441,6 +469,37 @@ int polarbp_awgn(const polarbp_code* c, uint64_t seed, uint64_t first_codeword, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "awgn launch");
     return POLARBP_OK;
+}
+
+int polarbp_decode_host_noalloc(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale,
+                                int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,
+                                int64_t* pe_updates, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (batch == 0) return POLARBP_OK;
+    const size_t need = host_layout(c->N, batch).total;
+    if (need > POLARBP_NOALLOC_SCRATCH_BYTES) {
+        size_t fit = 0;
+        size_t lo = 1, hi = (size_t)batch;
+        while (lo <= hi) {  // largest batch whose staging fits the array
+            const size_t mid = (lo + hi) / 2;
+            if (host_layout(c->N, (int)mid).total <= POLARBP_NOALLOC_SCRATCH_BYTES) {
+                fit = mid;
+                lo = mid + 1;
+            } else {
+                hi = mid - 1;
+            }
+        }
+        return fail(POLARBP_ERR_ARG, "batch too large for the built-in 16 MiB scratch: at most " +
+                                         std::to_string(fit) + " codewords of length " + std::to_string(c->N) +
+                                         " per call");
+    }
+    void* ws = nullptr;
+    int rc = noalloc_scratch_address(&ws);
+    if (rc != POLARBP_OK) return rc;
+    return polarbp_decode_host(c, llr, batch, max_iter, scale, stop_mode, freeze_mode, u_hat, iterations, pe_updates,
+                               ws, POLARBP_NOALLOC_SCRATCH_BYTES, stream);
 }
 
 int polarbp_get_status(const polarbp_code* c, void* stream)
