@@ -210,6 +210,68 @@ int polarbp_decode_host_noalloc(const polarbp_code* code, const float* llr, int 
                                 int64_t* pe_updates, void* stream);
 
 /*
+ * A run of codewords that share one code, for polarbp_decode_segments.
+ *   code        code of every codeword of the run; N >= 256.
+ *   llr         device [count][N] channel LLRs.
+ *   u_hat       device [count][N] decoded source bits.
+ *   iterations  device [count] int32, or NULL; pe_updates device [count] int64, or NULL.
+ */
+typedef struct polarbp_segment {
+    const polarbp_code* code;
+    const float* llr;
+    uint8_t* u_hat;
+    int32_t* iterations;
+    int64_t* pe_updates;
+    int count;
+} polarbp_segment;
+
+/* polarbp_decode_segments_workspace -- device workspace bytes polarbp_decode_segments needs (queue counters). */
+size_t polarbp_decode_segments_workspace(void);
+
+/*
+ * polarbp_decode_segments -- decode a mixed stream of codewords of different
+ * lengths and rates (the same decode as polarbp_decode, per codeword) with one
+ * persistent launch per code length.  Each block holds the code's
+ * codewords-per-block groups of threads; a group takes the next codeword from
+ * a device counter, stops it at its own G-matrix stop or freeze completion,
+ * then takes the next, so codewords retire independently.  The launches for
+ * different lengths run concurrently on library-owned side streams joined back
+ * to `stream`; the whole call may be captured into a CUDA graph (call it once
+ * uncaptured first: the first call per kernel sets attributes and queries
+ * occupancy).
+ *   segs, nseg   runs of codewords; at most 8 runs per code length, N in {256 .. 4096}.
+ *   workspace    device buffer of polarbp_decode_segments_workspace() bytes
+ *                (counters; zeroed by the call).  Calls sharing a workspace must
+ *                not overlap on the GPU.
+ * Errors: POLARBP_ERR_ARG, POLARBP_ERR_UNSUPPORTED (N < 256 or > 4096), POLARBP_ERR_CUDA.
+ */
+int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
+                            int freeze_mode, void* workspace, size_t workspace_bytes, void* stream);
+
+/* polarbp_set_codewords_per_block / polarbp_get_codewords_per_block -- codewords
+ * decoded side by side by one block of the persistent launch (1, 2 or 4, as
+ * thread and shared-memory limits allow for the code length). */
+int polarbp_set_codewords_per_block(polarbp_code* code, int codewords_per_block);
+int polarbp_get_codewords_per_block(const polarbp_code* code, int* codewords_per_block);
+
+/*
+ * polarbp_autotune -- time the persistent decode of a synthetic batch
+ * (BPSK/AWGN at 2.5 dB, about 8M LLRs) for every admissible codewords-per-block
+ * value with the given decode settings and keep the fastest in the handle.
+ * Allocates and frees temporary device memory; synchronises `stream`.
+ * Errors: POLARBP_ERR_ARG (K = 0), POLARBP_ERR_UNSUPPORTED, POLARBP_ERR_NOMEM, POLARBP_ERR_CUDA.
+ */
+int polarbp_autotune(polarbp_code* code, int max_iter, float scale, int stop_mode, int freeze_mode, void* stream);
+
+/*
+ * polarbp_awgn_ebn0 -- polarbp_awgn with one Eb/N0 per codeword:
+ *   ebn0_db  device [batch] float, the Eb/N0 (dB) of codeword first_codeword + b.
+ * The noise words and source bits are those of polarbp_awgn.
+ */
+int polarbp_awgn_ebn0(const polarbp_code* code, uint64_t seed, uint64_t first_codeword, int batch,
+                      const float* ebn0_db, uint8_t* u, float* llr, void* stream);
+
+/*
  * polarbp_get_status -- read and clear the handle's device status word.  Waits
  * for `stream`.  Returns POLARBP_ERR_NONFINITE when a decode since the last
  * call saw a non-finite LLR, else POLARBP_OK (or POLARBP_ERR_CUDA).

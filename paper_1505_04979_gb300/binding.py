@@ -57,6 +57,13 @@ _SIGS = {
                                                    ctypes.c_int, _VP, _VP, _VP, _VP]),
     "polarbp_awgn": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_float, _VP, _VP,
                                     _VP]),
+    "polarbp_awgn_ebn0": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "polarbp_decode_segments_workspace": (ctypes.c_size_t, []),
+    "polarbp_decode_segments": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                               ctypes.c_int, _VP, ctypes.c_size_t, _VP]),
+    "polarbp_set_codewords_per_block": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "polarbp_get_codewords_per_block": (ctypes.c_int, [_VP, _VP]),
+    "polarbp_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _VP]),
     "polarbp_get_status": (ctypes.c_int, [_VP, _VP]),
     "polarbp_last_error": (ctypes.c_char_p, []),
     "polarbp_version": (ctypes.c_char_p, []),
@@ -170,6 +177,75 @@ def polarbp_awgn(code: PolarCode, seed: int, first_codeword: int, batch: int, eb
     _check(lib().polarbp_awgn(code.handle, seed, first_codeword, batch, ebn0_db, _ptr(u), _ptr(llr),
                               _stream(stream)), "polarbp_awgn")
     return u, llr
+
+
+def polarbp_awgn_ebn0(code: PolarCode, seed: int, first_codeword: int, ebn0_db, u=None, llr=None,
+                      with_u: bool = True, stream=None):
+    """Device channel input with one Eb/N0 per codeword (``ebn0_db``: CUDA float32 [batch])."""
+    import torch
+    batch = ebn0_db.shape[0]
+    _need(ebn0_db, torch.float32, (batch,), "ebn0_db")
+    dev = ebn0_db.device
+    if llr is None:
+        llr = torch.empty((batch, code.N), dtype=torch.float32, device=dev)
+    if with_u and u is None:
+        u = torch.empty((batch, code.N), dtype=torch.uint8, device=dev)
+    _need(llr, torch.float32, (batch, code.N), "llr")
+    if u is not None:
+        _need(u, torch.uint8, (batch, code.N), "u")
+    _check(lib().polarbp_awgn_ebn0(code.handle, seed, first_codeword, batch, _ptr(ebn0_db), _ptr(u), _ptr(llr),
+                                   _stream(stream)), "polarbp_awgn_ebn0")
+    return u, llr
+
+
+class _Segment(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("u_hat", ctypes.c_void_p),
+                ("iterations", ctypes.c_void_p), ("pe_updates", ctypes.c_void_p), ("count", ctypes.c_int)]
+
+
+def polarbp_decode_segments_workspace() -> int:
+    return int(lib().polarbp_decode_segments_workspace())
+
+
+def polarbp_decode_segments(segments, max_iter: int, scale: float = 0.9375, stop_mode: int = 0,
+                            freeze_mode: int = 0, workspace=None, stream=None):
+    """Decode runs of codewords [(code, llr, u_hat, iterations, pe_updates), ...] with one
+    persistent launch per code length.  ``workspace``: CUDA uint8 tensor (allocated if None)."""
+    import torch
+    arr = (_Segment * max(1, len(segments)))()
+    for k, (code, llr, u_hat, it, pe) in enumerate(segments):
+        n = llr.shape[0]
+        _need(llr, torch.float32, (n, code.N), "llr")
+        _need(u_hat, torch.uint8, (n, code.N), "u_hat")
+        if it is not None:
+            _need(it, torch.int32, (n,), "iterations")
+        if pe is not None:
+            _need(pe, torch.int64, (n,), "pe_updates")
+        arr[k] = _Segment(code.handle.value, llr.data_ptr(), u_hat.data_ptr(), None if it is None else it.data_ptr(),
+                          None if pe is None else pe.data_ptr(), n)
+    if workspace is None:
+        workspace = torch.empty(polarbp_decode_segments_workspace(), dtype=torch.uint8, device="cuda")
+    _check(lib().polarbp_decode_segments(ctypes.cast(arr, ctypes.c_void_p), len(segments), max_iter, scale,
+                                         stop_mode, freeze_mode, _ptr(workspace), workspace.numel(),
+                                         _stream(stream)), "polarbp_decode_segments")
+    return workspace
+
+
+def polarbp_set_codewords_per_block(code: PolarCode, cpc: int) -> None:
+    _check(lib().polarbp_set_codewords_per_block(code.handle, cpc), "polarbp_set_codewords_per_block")
+
+
+def polarbp_get_codewords_per_block(code: PolarCode) -> int:
+    v = ctypes.c_int()
+    _check(lib().polarbp_get_codewords_per_block(code.handle, ctypes.byref(v)), "polarbp_get_codewords_per_block")
+    return v.value
+
+
+def polarbp_autotune(code: PolarCode, max_iter: int, scale: float = 0.9375, stop_mode: int = 1,
+                     freeze_mode: int = 1, stream=None) -> int:
+    _check(lib().polarbp_autotune(code.handle, max_iter, scale, stop_mode, freeze_mode, _stream(stream)),
+           "polarbp_autotune")
+    return polarbp_get_codewords_per_block(code)
 
 
 def polarbp_decode(code: PolarCode, llr, max_iter: int, scale: float = 0.9375, stop_mode: int = 0,

@@ -132,7 +132,34 @@ struct DecodeArgs {
     float alpha;
 };
 
-enum : int { CTL_P = 0, CTL_DONE = 1, CTL_EVENT = 2, CTL_PE = 4, CTL_EV = 8 };
+// Pointers of one codeword (trace pointers already offset to the codeword).
+struct CwIO {
+    const float* llr;              // [N]
+    const uint32_t* frozen_words;  // ceil(N/32) words
+    uint8_t* u_hat;                // [N]
+    int32_t* iters;                // one entry, or NULL
+    int64_t* pe;                   // one entry, or NULL
+    float* trace_L;                // [max_iter][M+1][N], or NULL
+    float* trace_R;
+    int32_t* trace_P;              // [max_iter]
+};
+
+enum : int { CTL_P = 0, CTL_DONE = 1, CTL_EVENT = 2, CTL_Q = 3, CTL_PE = 4, CTL_EV = 8 };
+
+// Barrier of the CPC-way group of threads that decodes one codeword: the whole
+// block when it decodes one codeword, a warp when the group is a warp, else a
+// named barrier per group (ids 1..CPC; id 0 is __syncthreads).
+template <int BLOCK, int CPC>
+__device__ __forceinline__ void group_sync(int grp)
+{
+    if constexpr (CPC == 1) {
+        __syncthreads();
+    } else if constexpr (BLOCK == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(BLOCK) : "memory");
+    }
+}
 
 template <int M>
 struct SmemLayout {
@@ -614,8 +641,8 @@ __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb,
 }
 
 template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE>
-__device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha,
-                                          const DecodeArgs& a, long long trace_base)
+__device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha, const CwIO& a,
+                                          long long trace_base)
 {
     using G = Geo<M>;
     constexpr int N = G::N, EL = G::EL;
@@ -673,9 +700,9 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     if constexpr (Q + 1 < G::cnt(PH)) run_stage<M, PH, Q + 1, GSTOP, FREEZE, TRACE>(rg, sm, tid, P0, alpha, a, trace_base);
 }
 
-template <int M, int PH, bool GSTOP, bool FREEZE, bool TRACE>
+template <int M, int PH, bool GSTOP, bool FREEZE, bool TRACE, int CPC>
 __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, int P0, float alpha,
-                                          const DecodeArgs& a, long long trace_base)
+                                          const CwIO& a, long long trace_base, int grp)
 {
     using G = Geo<M>;
     constexpr int N = G::N, EL = G::EL;
@@ -695,8 +722,8 @@ __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, boo
 #pragma unroll
             for (int e = 0; e < EL; ++e) sm.Rx[(PH & 1) * G::BUF + pb + padded_off<M, PH, SH>(e)] = rg.R[e];
         }
-        __syncthreads();
-        run_phase<M, PH + 1, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
+        group_sync<G::BLOCK, CPC>(grp);
+        run_phase<M, PH + 1, GSTOP, FREEZE, TRACE, CPC>(rg, sm, tid, worker, P0, alpha, a, trace_base, grp);
     }
 }
 
@@ -730,14 +757,14 @@ __device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, 
 }
 
 template <int M, int C>
-__device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, const DecodeArgs& a,
+__device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, const CwIO& a,
                                                 long long trace_base)
 {
     using G = Geo<M>;
     if constexpr (C <= M) {
         if constexpr (G::is_boundary(C)) {
             constexpr int SH = G::padsh(G::bslot(C));
-            for (int i = tid; i < G::N; i += blockDim.x)
+            for (int i = tid; i < G::N; i += G::BLOCK)
                 a.trace_L[trace_base + (long long)C * G::N + i] = sm.Lb[G::bslot(C) * G::BUF + padded<SH>(i)];
         } else if (worker) {
 #pragma unroll
@@ -748,27 +775,26 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
     }
 }
 
-template <int M, bool GSTOP, bool FREEZE, bool TRACE>
-__global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_kernel(DecodeArgs a)
+// Decode one codeword with the BLOCK threads of group grp (tid = thread index in
+// the group) on the group's shared memory smem_raw.
+template <int M, bool GSTOP, bool FREEZE, bool TRACE, int CPC>
+__device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, float alpha, unsigned int* status,
+                                                unsigned char* smem_raw, int tid, int grp)
 {
     using G = Geo<M>;
     constexpr int N = G::N, EL = G::EL, T = G::T, NW = G::NW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<M> sm(smem_raw);
-    const int tid = threadIdx.x;
     const int lane = tid & 31;
     const bool worker = tid < T;
-    const long long cw = blockIdx.x;
-    const float alpha = a.alpha;
 
-    for (int w = tid; w < NW; w += blockDim.x) {
+    for (int w = tid; w < NW; w += G::BLOCK) {
         sm.Fz[w] = a.frozen_words[w];
         sm.U[w] = 0u;
     }
-    for (int i = tid; i < G::NB * G::BUF; i += blockDim.x) sm.Lb[i] = 0.f;
+    for (int i = tid; i < G::NB * G::BUF; i += G::BLOCK) sm.Lb[i] = 0.f;
     {
         uint32_t* hd32 = reinterpret_cast<uint32_t*>(sm.hd);
-        for (int i = tid; i < (int)(SmemLayout<M>::hd_bytes / 4); i += blockDim.x) hd32[i] = 0u;
+        for (int i = tid; i < (int)(SmemLayout<M>::hd_bytes / 4); i += G::BLOCK) hd32[i] = 0u;
     }
     if (tid == 0) {
         sm.ctl[CTL_P] = 0;
@@ -776,18 +802,18 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
         sm.ctl[CTL_EVENT] = 0;
         *sm.pe_acc() = 0;
     }
-    __syncthreads();
+    group_sync<G::BLOCK, CPC>(grp);
 
     Regs<M> rg;
     if (worker) {
         bool finite = true;
 #pragma unroll
         for (int e = 0; e < EL; ++e) {
-            const float v = a.llr[cw * N + elem_index<M, 0>(tid, e)];
+            const float v = a.llr[elem_index<M, 0>(tid, e)];
             finite &= isfinite(v);
             sm.llr[e * T + tid] = v;
         }
-        if (!finite) atomicOr(a.status, 1u);
+        if (!finite) atomicOr(status, 1u);
 #pragma unroll
         for (int c = 0; c < G::NR; ++c)
 #pragma unroll
@@ -801,9 +827,9 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
     }
 
     int it = 1;
-    for (; it <= a.max_iter; ++it) {
+    for (; it <= max_iter; ++it) {
         const int P0 = sm.ctl[CTL_P];
-        const long long trace_base = TRACE ? (cw * a.max_iter + (it - 1)) * (long long)(M + 1) * N : 0;
+        const long long trace_base = TRACE ? (long long)(it - 1) * (M + 1) * N : 0;
         if (worker) {
 #pragma unroll
             for (int e = 0; e < EL; ++e) rg.R[e] = sm.llr[e * T + tid];
@@ -812,12 +838,12 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
                 for (int e = 0; e < EL; ++e) a.trace_R[trace_base + elem_index<M, 0>(tid, e)] = rg.R[e];
             }
         }
-        run_phase<M, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, worker, P0, alpha, a, trace_base);
-        __syncthreads();
+        run_phase<M, 0, GSTOP, FREEZE, TRACE, CPC>(rg, sm, tid, worker, P0, alpha, a, trace_base, grp);
+        group_sync<G::BLOCK, CPC>(grp);
         bool done = false;
         if constexpr (GSTOP || FREEZE) {
             if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane);
-            __syncthreads();
+            group_sync<G::BLOCK, CPC>(grp);
             done = sm.ctl[CTL_DONE] != 0;
             if constexpr (FREEZE) {
                 const int mask = sm.ctl[CTL_EVENT];
@@ -825,13 +851,13 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
             }
         }
         if constexpr (TRACE) {
-            __syncthreads();
+            group_sync<G::BLOCK, CPC>(grp);
             trace_L_columns<M, 1>(rg, sm, tid, worker, a, trace_base);
-            if (tid == 0) a.trace_P[cw * a.max_iter + (it - 1)] = sm.ctl[CTL_P];
+            if (tid == 0) a.trace_P[it - 1] = sm.ctl[CTL_P];
         }
         if (done) break;
     }
-    const int iters = it <= a.max_iter ? it : a.max_iter;
+    const int iters = it <= max_iter ? it : max_iter;
 
     // output: stored bits on covered positions, HD(R[M]) elsewhere, 0 on frozen
     if (worker) {
@@ -850,14 +876,92 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_k
             uint8_t bit;
             if (i < P) bit = (uint8_t)bit_of(sm.U, i);
             else bit = bit_of(sm.Fz, i) ? 0 : (uint8_t)((hdM >> e) & 1u);
-            a.u_hat[cw * N + i] = bit;
+            a.u_hat[i] = bit;
         }
     }
     if (tid == 0) {
-        if (a.iters) a.iters[cw] = iters;
-        if (a.pe) a.pe[cw] = (GSTOP || FREEZE) ? *sm.pe_acc() : (long long)iters * M * (N >> 1);
+        if (a.iters) *a.iters = iters;
+        if (a.pe) *a.pe = (GSTOP || FREEZE) ? *sm.pe_acc() : (long long)iters * M * (N >> 1);
     }
 }
+
+// One codeword per block, grid = batch.
+template <int M, bool GSTOP, bool FREEZE, bool TRACE>
+__global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_kernel(DecodeArgs a)
+{
+    constexpr int N = Geo<M>::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const long long cw = blockIdx.x;
+    const long long tb = TRACE ? cw * a.max_iter * (long long)(M + 1) * N : 0;
+    const CwIO io{a.llr + cw * N,
+                  a.frozen_words,
+                  a.u_hat + cw * N,
+                  a.iters ? a.iters + cw : nullptr,
+                  a.pe ? a.pe + cw : nullptr,
+                  TRACE ? a.trace_L + tb : nullptr,
+                  TRACE ? a.trace_R + tb : nullptr,
+                  TRACE ? a.trace_P + cw * a.max_iter : nullptr};
+    decode_codeword<M, GSTOP, FREEZE, TRACE, 1>(io, a.max_iter, a.alpha, a.status, smem_raw, threadIdx.x, 0);
+}
+
+// Persistent decoding of a queue of codewords split in segments (one code per
+// segment, all of length N = 2^M): CPC groups of threads per block, each group
+// takes the next codeword from a device counter, decodes it and retires it at
+// its own stop, then takes the next, until the queue is empty.
+constexpr int kMaxSeg = 8;
+struct SegArgs {
+    int nseg;
+    int total;
+    int* queue;  // device counter, zero at launch
+    int max_iter;
+    float alpha;
+    unsigned int* status;
+    int start[kMaxSeg + 1];  // first queue index of each segment; start[nseg] = total
+    const float* llr[kMaxSeg];
+    const uint32_t* frozen_words[kMaxSeg];
+    uint8_t* u_hat[kMaxSeg];
+    int32_t* iters[kMaxSeg];
+    int64_t* pe[kMaxSeg];
+};
+
+template <int M, int CPC>
+struct PersistentShape {
+    static constexpr int THREADS = Geo<M>::BLOCK * CPC;
+    static constexpr int MIN_BLOCKS = (640 / THREADS) < 1 ? 1 : (640 / THREADS);
+};
+
+template <int M, bool GSTOP, bool FREEZE, int CPC>
+__global__ void __launch_bounds__(PersistentShape<M, CPC>::THREADS, PersistentShape<M, CPC>::MIN_BLOCKS)
+    bp_decode_persistent(SegArgs a)
+{
+    using G = Geo<M>;
+    constexpr int N = G::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / G::BLOCK;
+    const int tid = threadIdx.x % G::BLOCK;
+    unsigned char* smem = smem_raw + grp * SmemLayout<M>::bytes;
+    int* qslot = reinterpret_cast<int*>(smem + SmemLayout<M>::off_Ctl) + CTL_Q;
+    for (;;) {
+        group_sync<G::BLOCK, CPC>(grp);  // the previous codeword's readers are done with smem
+        if (tid == 0) *qslot = atomicAdd(a.queue, 1);
+        group_sync<G::BLOCK, CPC>(grp);
+        const int q = *qslot;
+        if (q >= a.total) break;
+        int sg = 0;
+        while (sg + 1 < a.nseg && q >= a.start[sg + 1]) ++sg;
+        const long long r = q - a.start[sg];
+        const CwIO io{a.llr[sg] + r * N,
+                      a.frozen_words[sg],
+                      a.u_hat[sg] + r * N,
+                      a.iters[sg] ? a.iters[sg] + r : nullptr,
+                      a.pe[sg] ? a.pe[sg] + r : nullptr,
+                      nullptr,
+                      nullptr,
+                      nullptr};
+        decode_codeword<M, GSTOP, FREEZE, false, CPC>(io, a.max_iter, a.alpha, a.status, smem, tid, grp);
+    }
+}
+
 
 struct LaunchReq {
     DecodeArgs args;
@@ -894,6 +998,94 @@ cudaError_t launch_decode(const LaunchReq& q)
     if (g) return launch_one<M, true, false, false>(q);
     if (f) return launch_one<M, false, true, false>(q);
     return launch_one<M, false, false, false>(q);
+}
+
+
+// ---------------------------------------------------------------------------
+// persistent launches
+// ---------------------------------------------------------------------------
+struct SegLaunch {
+    SegArgs args;
+    int stop_mode;
+    int freeze_mode;
+    int cpc;
+    int sms;
+    cudaStream_t stream;
+};
+
+template <int M, int CPC>
+constexpr bool persistent_fits()
+{
+    return PersistentShape<M, CPC>::THREADS <= 512 && SmemLayout<M>::bytes * CPC <= 200 * 1024;
+}
+
+template <int M, bool GSTOP, bool FREEZE, int CPC>
+cudaError_t launch_persistent_one(const SegLaunch& q)
+{
+    auto kern = bp_decode_persistent<M, GSTOP, FREEZE, CPC>;
+    constexpr size_t smem = SmemLayout<M>::bytes * CPC;
+    constexpr int threads = PersistentShape<M, CPC>::THREADS;
+    static int blocks_per_sm = 0;  // one value per instantiation (same on every GB300)
+    if (blocks_per_sm == 0) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        blocks_per_sm = b > 0 ? b : 1;
+    }
+    long long grid = (long long)blocks_per_sm * q.sms;
+    const long long need = (q.args.total + CPC - 1) / CPC;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, threads, smem, q.stream>>>(q.args);
+    return cudaGetLastError();
+}
+
+template <int M, int CPC>
+cudaError_t launch_persistent_cpc(const SegLaunch& q)
+{
+    if constexpr (!persistent_fits<M, CPC>()) {
+        (void)q;
+        return cudaErrorInvalidConfiguration;
+    } else {
+        const bool g = q.stop_mode != 0, f = q.freeze_mode != 0;
+        if (g && f) return launch_persistent_one<M, true, true, CPC>(q);
+        if (g) return launch_persistent_one<M, true, false, CPC>(q);
+        if (f) return launch_persistent_one<M, false, true, CPC>(q);
+        return launch_persistent_one<M, false, false, CPC>(q);
+    }
+}
+
+template <int M>
+bool persistent_supported_m(int cpc)
+{
+    return cpc == 1 ? persistent_fits<M, 1>() : cpc == 2 ? persistent_fits<M, 2>() : cpc == 4 ? persistent_fits<M, 4>() : false;
+}
+
+inline bool persistent_supported(int m, int cpc)
+{
+    switch (m) {
+    case 8: return persistent_supported_m<8>(cpc);
+    case 9: return persistent_supported_m<9>(cpc);
+    case 10: return persistent_supported_m<10>(cpc);
+    case 11: return persistent_supported_m<11>(cpc);
+    case 12: return persistent_supported_m<12>(cpc);
+    default: return false;
+    }
+}
+
+template <int M>
+cudaError_t launch_persistent(const SegLaunch& q)
+{
+    switch (q.cpc) {
+    case 1: return launch_persistent_cpc<M, 1>(q);
+    case 2: return launch_persistent_cpc<M, 2>(q);
+    case 4: return launch_persistent_cpc<M, 4>(q);
+    default: return cudaErrorInvalidConfiguration;
+    }
 }
 
 }  // namespace polarbp

@@ -21,6 +21,7 @@ struct polarbp_code {
     std::vector<uint8_t> frozen;
     uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
     unsigned int* d_status = nullptr;
+    int cpc = 1;  // codewords per block of the persistent launch
 };
 
 // decode kernels, one translation unit per code length (compiled in parallel)
@@ -37,6 +38,11 @@ cudaError_t launch_m9(const LaunchReq&);
 cudaError_t launch_m10(const LaunchReq&);
 cudaError_t launch_m11(const LaunchReq&);
 cudaError_t launch_m12(const LaunchReq&);
+cudaError_t launch_persistent_m8(const SegLaunch&);
+cudaError_t launch_persistent_m9(const SegLaunch&);
+cudaError_t launch_persistent_m10(const SegLaunch&);
+cudaError_t launch_persistent_m11(const SegLaunch&);
+cudaError_t launch_persistent_m12(const SegLaunch&);
 }  // namespace polarbp
 
 namespace {
@@ -152,11 +158,14 @@ __device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint64_t cw, uint
 
 // One block per codeword: source bits, encoder (as encode_kernel), BPSK + AWGN.
 __global__ void awgn_kernel(const uint32_t* __restrict__ frozen_words, int N, int m, uint64_t seed, uint64_t first,
-                            float sigma, uint8_t* __restrict__ u_out, float* __restrict__ llr)
+                            float sigma_all, const float* __restrict__ ebn0_per_cw, float rate,
+                            uint8_t* __restrict__ u_out, float* __restrict__ llr)
 {
     extern __shared__ uint8_t bits[];
     const long long b = blockIdx.x;
     const uint64_t cw = first + (uint64_t)b;
+    // per-codeword Eb/N0: sigma^2 = 1 / (2 R 10^(Eb/N0 / 10))
+    const float sigma = ebn0_per_cw ? sqrtf(1.f / (2.f * rate * exp10f(ebn0_per_cw[b] * 0.1f))) : sigma_all;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const uint32_t word = philox_word(seed, cw, 1u, (uint32_t)(i >> 5));
         const uint32_t fz = (frozen_words[i >> 5] >> (i & 31)) & 1u;
@@ -257,6 +266,54 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     }
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     return POLARBP_OK;
+}
+
+// Side streams and events for the concurrent persistent launches of
+// polarbp_decode_segments, created once per device.
+constexpr int kSegWorkspace = 256;
+constexpr int kSideStreams = 4;
+struct SideResources {
+    bool ready = false;
+    int sms = 0;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kSideStreams] = {};
+};
+std::mutex g_side_mutex;
+SideResources g_side[64];
+
+int side_resources(SideResources** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(POLARBP_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_side_mutex);
+    SideResources& r = g_side[dev];
+    if (!r.ready) {
+        e = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int k = 0; e == cudaSuccess && k < kSideStreams; ++k) {
+            e = cudaStreamCreateWithFlags(&r.side[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.join[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "side stream creation");
+        r.ready = true;
+    }
+    *out = &r;
+    return POLARBP_OK;
+}
+
+cudaError_t launch_persistent_m(int m, const polarbp::SegLaunch& q)
+{
+    switch (m) {
+    case 8: return polarbp::launch_persistent_m8(q);
+    case 9: return polarbp::launch_persistent_m9(q);
+    case 10: return polarbp::launch_persistent_m10(q);
+    case 11: return polarbp::launch_persistent_m11(q);
+    case 12: return polarbp::launch_persistent_m12(q);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // Staging area of polarbp_decode_host_noalloc: a fixed device array that is
@@ -465,7 +522,8 @@ int polarbp_awgn(const polarbp_code* c, uint64_t seed, uint64_t first_codeword, 
     const float sigma = (float)std::sqrt(1.0 / (2.0 * rate * std::pow(10.0, ebn0_db / 10.0)));
     const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
     awgn_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(c->d_frozen, c->N, c->m, seed,
-                                                                             first_codeword, sigma, u, llr);
+                                                                             first_codeword, sigma, nullptr, 0.f, u,
+                                                                             llr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "awgn launch");
     return POLARBP_OK;
@@ -500,6 +558,185 @@ int polarbp_decode_host_noalloc(const polarbp_code* c, const float* llr, int bat
     if (rc != POLARBP_OK) return rc;
     return polarbp_decode_host(c, llr, batch, max_iter, scale, stop_mode, freeze_mode, u_hat, iterations, pe_updates,
                                ws, POLARBP_NOALLOC_SCRATCH_BYTES, stream);
+}
+
+size_t polarbp_decode_segments_workspace(void) { return kSegWorkspace; }
+
+int polarbp_set_codewords_per_block(polarbp_code* c, int cpc)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (!polarbp::persistent_supported(c->m, cpc))
+        return fail(POLARBP_ERR_UNSUPPORTED, "codewords per block not admissible for this code length");
+    c->cpc = cpc;
+    return POLARBP_OK;
+}
+
+int polarbp_get_codewords_per_block(const polarbp_code* c, int* cpc)
+{
+    if (!c || !cpc) return fail(POLARBP_ERR_ARG, "NULL argument");
+    *cpc = c->cpc;
+    return POLARBP_OK;
+}
+
+int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
+                            int freeze_mode, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (nseg < 0 || (nseg > 0 && !segs)) return fail(POLARBP_ERR_ARG, "bad segment list");
+    if (max_iter < 1) return fail(POLARBP_ERR_ARG, "max_iter must be >= 1");
+    if (!(scale > 0.f) || !std::isfinite(scale)) return fail(POLARBP_ERR_ARG, "scale must be finite and > 0");
+    if (stop_mode != POLARBP_STOP_NONE && stop_mode != POLARBP_STOP_GMATRIX)
+        return fail(POLARBP_ERR_ARG, "unknown stop_mode");
+    if (freeze_mode != POLARBP_FREEZE_OFF && freeze_mode != POLARBP_FREEZE_CSFG)
+        return fail(POLARBP_ERR_ARG, "unknown freeze_mode");
+    if (!workspace || workspace_bytes < (size_t)kSegWorkspace) return fail(POLARBP_ERR_ARG, "workspace too small");
+    std::vector<int> by_m[13];
+    for (int k = 0; k < nseg; ++k) {
+        const polarbp_segment& g = segs[k];
+        if (!g.code) return fail(POLARBP_ERR_ARG, "segment without a code");
+        if (g.code->m < 8 || g.code->m > 12)
+            return fail(POLARBP_ERR_UNSUPPORTED, "segments support N from 256 to 4096");
+        if (g.count < 0) return fail(POLARBP_ERR_ARG, "segment count must be >= 0");
+        if (g.count == 0) continue;
+        if (!g.llr || !g.u_hat) return fail(POLARBP_ERR_ARG, "segment llr and u_hat must be device pointers");
+        int rc = check_device(g.code);
+        if (rc != POLARBP_OK) return rc;
+        by_m[g.code->m].push_back(k);
+    }
+    SideResources* side = nullptr;
+    int rc = side_resources(&side);
+    if (rc != POLARBP_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, kSegWorkspace, s);
+    if (e != cudaSuccess) return cuda_fail(e, "segment counters");
+    std::vector<int> ms;
+    for (int m = 8; m <= 12; ++m) {
+        if (by_m[m].empty()) continue;
+        if ((int)by_m[m].size() > polarbp::kMaxSeg) return fail(POLARBP_ERR_ARG, "at most 8 segments per code length");
+        long long total = 0;
+        for (int k : by_m[m]) total += segs[k].count;
+        if (total > 0x7fffffffLL) return fail(POLARBP_ERR_ARG, "too many codewords of one length");
+        const int cpc = segs[by_m[m][0]].code->cpc;
+        if (!polarbp::persistent_supported(m, cpc)) return fail(POLARBP_ERR_UNSUPPORTED, "codewords per block");
+        ms.push_back(m);
+    }
+    if (ms.empty()) return POLARBP_OK;
+    if (ms.size() > 1) {
+        e = cudaEventRecord(side->fork, s);
+        for (size_t g = 1; e == cudaSuccess && g < ms.size(); ++g) e = cudaStreamWaitEvent(side->side[g - 1], side->fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+    }
+    for (size_t g = 0; g < ms.size(); ++g) {
+        const int m = ms[g];
+        polarbp::SegLaunch q{};
+        q.args.nseg = (int)by_m[m].size();
+        q.args.queue = static_cast<int*>(workspace) + m;
+        q.args.max_iter = max_iter;
+        q.args.alpha = scale;
+        q.args.status = segs[by_m[m][0]].code->d_status;
+        int start = 0;
+        for (int j = 0; j < q.args.nseg; ++j) {
+            const polarbp_segment& sg = segs[by_m[m][j]];
+            q.args.start[j] = start;
+            q.args.llr[j] = sg.llr;
+            q.args.frozen_words[j] = sg.code->d_frozen;
+            q.args.u_hat[j] = sg.u_hat;
+            q.args.iters[j] = sg.iterations;
+            q.args.pe[j] = sg.pe_updates;
+            start += sg.count;
+        }
+        q.args.start[q.args.nseg] = start;
+        q.args.total = start;
+        q.stop_mode = stop_mode;
+        q.freeze_mode = freeze_mode;
+        q.cpc = segs[by_m[m][0]].code->cpc;
+        q.sms = side->sms;
+        q.stream = g == 0 ? s : side->side[g - 1];
+        e = launch_persistent_m(m, q);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent decode launch");
+    }
+    for (size_t g = 1; g < ms.size(); ++g) {
+        e = cudaEventRecord(side->join[g - 1], side->side[g - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side->join[g - 1], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "stream join");
+    }
+    return POLARBP_OK;
+}
+
+int polarbp_autotune(polarbp_code* c, int max_iter, float scale, int stop_mode, int freeze_mode, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (c->m < 8 || c->m > 12) return fail(POLARBP_ERR_UNSUPPORTED, "autotune supports N from 256 to 4096");
+    if (c->K < 1) return fail(POLARBP_ERR_ARG, "autotune needs K >= 1");
+    const int B = std::max(2048, std::min(65536, (1 << 23) >> c->m));
+    const size_t n = (size_t)B * c->N;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* d_llr = nullptr;
+    uint8_t* d_u = nullptr;
+    void* ws = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&d_llr, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d_u, n);
+    if (e == cudaSuccess) e = cudaMalloc(&ws, kSegWorkspace);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int rc = POLARBP_OK;
+    if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? fail(POLARBP_ERR_NOMEM, "autotune buffers")
+                                                                 : cuda_fail(e, "autotune setup");
+    const int keep = c->cpc;
+    int best = keep;
+    float best_ms = 3.4e38f;
+    if (rc == POLARBP_OK) rc = polarbp_awgn(c, 1, 0, B, 2.5f, nullptr, d_llr, stream);
+    for (int cpc : {1, 2, 4}) {
+        if (rc != POLARBP_OK) break;
+        if (!polarbp::persistent_supported(c->m, cpc)) continue;
+        c->cpc = cpc;
+        polarbp_segment sg{c, d_llr, d_u, nullptr, nullptr, B};
+        rc = polarbp_decode_segments(&sg, 1, max_iter, scale, stop_mode, freeze_mode, ws, kSegWorkspace, stream);
+        if (rc != POLARBP_OK) break;
+        e = cudaEventRecord(e0, s);
+        for (int rep = 0; e == cudaSuccess && rep < 3; ++rep) {
+            rc = polarbp_decode_segments(&sg, 1, max_iter, scale, stop_mode, freeze_mode, ws, kSegWorkspace, stream);
+            if (rc != POLARBP_OK) break;
+        }
+        if (rc != POLARBP_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cpc;
+        }
+    }
+    c->cpc = rc == POLARBP_OK ? best : keep;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_llr);
+    cudaFree(d_u);
+    cudaFree(ws);
+    return rc;
+}
+
+int polarbp_awgn_ebn0(const polarbp_code* c, uint64_t seed, uint64_t first_codeword, int batch, const float* ebn0_db,
+                      uint8_t* u, float* llr, void* stream)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (c->K < 1) return fail(POLARBP_ERR_ARG, "the channel needs K >= 1 (rate > 0)");
+    if (batch == 0) return POLARBP_OK;
+    if (!llr || !ebn0_db) return fail(POLARBP_ERR_ARG, "llr and ebn0_db must be device pointers");
+    int rc = check_device(c);
+    if (rc != POLARBP_OK) return rc;
+    const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
+    awgn_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(
+        c->d_frozen, c->N, c->m, seed, first_codeword, 0.f, ebn0_db, (float)c->K / (float)c->N, u, llr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "awgn launch");
+    return POLARBP_OK;
 }
 
 int polarbp_get_status(const polarbp_code* c, void* stream)

@@ -27,6 +27,7 @@ _MASK32 = np.uint64(0xFFFFFFFF)
 # stream identifiers
 STREAM_INFO = 1
 STREAM_NOISE = 2
+STREAM_DRAW = 3
 
 DEFAULT_SEED = 1505049790
 
@@ -106,13 +107,29 @@ def gaussian(seed: int, cw_index, N: int) -> np.ndarray:
     return z[:, :N]
 
 
-def sigma(ebn0_db: float, rate: float) -> float:
-    """AWGN standard deviation for BPSK at Eb/N0 (dB) and code rate K/N."""
-    return math.sqrt(1.0 / (2.0 * rate * 10.0 ** (ebn0_db / 10.0)))
+def uniform(seed: int, cw_index, lo: float, hi: float, which: int = 0) -> np.ndarray:
+    """One uniform draw in [lo, hi) per codeword (stream 3, word `which`), float64."""
+    w = random_words(seed, STREAM_DRAW, cw_index, which + 1)[:, which].astype(np.float64)
+    return lo + (hi - lo) * w * (1.0 / 4294967296.0)
 
 
-def channel_llr(x: np.ndarray, z: np.ndarray, sig: float) -> np.ndarray:
-    """BPSK (0 -> +1, 1 -> -1) plus noise sig*z; LLR = 2y/sig^2 rounded to binary32."""
+def choice(seed: int, cw_index, n: int, which: int = 0) -> np.ndarray:
+    """One index in [0, n) per codeword (stream 3, word `which`)."""
+    w = random_words(seed, STREAM_DRAW, cw_index, which + 1)[:, which].astype(np.uint64)
+    return (w % np.uint64(n)).astype(np.int64)
+
+
+def sigma(ebn0_db, rate: float):
+    """AWGN standard deviation for BPSK at Eb/N0 (dB, scalar or array) and code rate K/N."""
+    return np.sqrt(1.0 / (2.0 * rate * 10.0 ** (np.asarray(ebn0_db, np.float64) / 10.0)))
+
+
+def channel_llr(x: np.ndarray, z: np.ndarray, sig) -> np.ndarray:
+    """BPSK (0 -> +1, 1 -> -1) plus noise sig*z; LLR = 2y/sig^2 rounded to binary32.
+    ``sig`` is a scalar or one value per codeword (row)."""
+    sig = np.asarray(sig, np.float64)
+    if sig.ndim == 1:
+        sig = sig[:, None]
     y = (1.0 - 2.0 * np.asarray(x, np.float64)) + sig * np.asarray(z, np.float64)
     return (2.0 * y / (sig * sig)).astype(np.float32)
 

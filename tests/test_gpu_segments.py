@@ -1,0 +1,142 @@
+"""Persistent decoding of a mixed stream (polarbp_decode_segments): codewords of
+lengths 256 / 1024 / 4096 and rates 1/4, 1/2, 3/4 at per-codeword Eb/N0 in
+[1.5, 3.5] dB, in one call, against the binary32 oracle codeword by codeword."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04979_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CLASSES = [(256, 64), (256, 128), (256, 192), (1024, 256), (1024, 512), (1024, 768), (4096, 1024), (4096, 2048),
+           (4096, 3072)]
+ALPHA = 0.9375
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_04979_gb300 import build
+    build.build()
+    from paper_1505_04979_gb300 import binding
+    torch.cuda.set_device(0)
+    return binding
+
+
+def class_inputs(N, K, idx, seed):
+    fz = O.bec_frozen(N, K)
+    u = I.info_bits(seed, idx, fz)
+    x = O.encode(u)
+    ebn0 = I.uniform(seed, idx, 1.5, 3.5)
+    llr = I.channel_llr(x, I.gaussian(seed, idx, N), I.sigma(ebn0, K / N))
+    return fz, llr
+
+
+def run_segments(B, codes, llrs, max_iter, mode, **kw):
+    segs, outs = [], []
+    for code, llr in zip(codes, llrs):
+        n = llr.shape[0]
+        d = torch.from_numpy(llr).cuda()
+        uh = torch.empty((n, code.N), dtype=torch.uint8, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        pe = torch.empty(n, dtype=torch.int64, device="cuda")
+        segs.append((code, d, uh, it, pe))
+        outs.append((uh, it, pe))
+    B.polarbp_decode_segments(segs, max_iter, ALPHA, *mode, **kw)
+    torch.cuda.synchronize()
+    return segs, [tuple(t.cpu().numpy() for t in o) for o in outs]
+
+
+@pytest.mark.parametrize("mode", [(1, 1), (1, 0), (0, 1), (0, 0)])
+@pytest.mark.parametrize("cpc", [1, 2, 4])
+def test_mixed_segments_match_binary32_oracle(B, mode, cpc):
+    counts = [40, 40, 40, 24, 24, 24, 6, 6, 6]
+    codes, llrs, fzs = [], [], []
+    first = 0
+    for (N, K), n in zip(CLASSES, counts):
+        code = B.polarbp_construct(N, K)
+        try:
+            B.polarbp_set_codewords_per_block(code, cpc)
+        except B.PolarBPError:
+            pass  # not admissible at this length: keep the default
+        fz, llr = class_inputs(N, K, np.arange(first, first + n), 77)
+        first += n
+        codes.append(code)
+        llrs.append(llr)
+        fzs.append(fz)
+    _, outs = run_segments(B, codes, llrs, 30, mode)
+    for fz, llr, (uh, it, pe) in zip(fzs, llrs, outs):
+        ouh, oit, ope, _ = O.decode_batch(fz, llr, 30, ALPHA, mode[0], mode[1], fp32=True)
+        assert np.array_equal(it, oit) and np.array_equal(pe, ope) and np.array_equal(uh, ouh)
+
+
+def test_segments_graph_capture_and_replay(B):
+    codes, llrs = [], []
+    for (N, K), n in zip(CLASSES[::2], [64, 32, 16, 8, 4]):
+        codes.append(B.polarbp_construct(N, K))
+        llrs.append(class_inputs(N, K, np.arange(n), 5)[1])
+    segs, ref = run_segments(B, codes, llrs, 40, (1, 1))
+    for _, _, uh, it, pe in segs:
+        uh.zero_(), it.zero_(), pe.zero_()
+    ws = torch.empty(B.polarbp_decode_segments_workspace(), dtype=torch.uint8, device="cuda")
+    B.polarbp_decode_segments(segs, 40, ALPHA, 1, 1, workspace=ws)  # first call outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.polarbp_decode_segments(segs, 40, ALPHA, 1, 1, workspace=ws, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        for _, _, uh, it, pe in segs:
+            uh.zero_(), it.zero_(), pe.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for (_, _, uh, it, pe), r in zip(segs, ref):
+            assert np.array_equal(uh.cpu().numpy(), r[0]) and np.array_equal(it.cpu().numpy(), r[1])
+            assert np.array_equal(pe.cpu().numpy(), r[2])
+
+
+@pytest.mark.parametrize("N", [256, 1024, 4096])
+def test_autotune_picks_an_admissible_value(B, N):
+    code = B.polarbp_construct(N, N // 2)
+    cpc = B.polarbp_autotune(code, 40)
+    assert cpc in (1, 2, 4)
+    B.polarbp_set_codewords_per_block(code, cpc)
+
+
+def test_mixed_full_size_sampled(B):
+    """The mixed-stream configuration at full size: 2^20 codewords, each drawing its length
+    from {256, 1024, 4096}, its rate from {1/4, 1/2, 3/4} and its Eb/N0 from U[1.5, 3.5] dB,
+    decoded with G-matrix stop and freezing (max 60 iterations) in one call with autotuned
+    codewords per block.  Bulk inputs come from the device generator; 6 rows of every class
+    are overwritten with host-generated inputs and checked against the binary32 oracle."""
+    total = 1 << 20
+    seed = 1505049792
+    idx = np.arange(total)
+    cls = I.choice(seed, idx, 9, which=1)
+    segs, host_rows, checks = [], [], []
+    for k, (N, K) in enumerate(CLASSES):
+        members = idx[cls == k]
+        code = B.polarbp_construct(N, K)
+        B.polarbp_autotune(code, 60)
+        ebn0 = torch.from_numpy(I.uniform(seed, members, 1.5, 3.5).astype(np.float32)).cuda()
+        _, llr = B.polarbp_awgn_ebn0(code, seed, 0, ebn0, with_u=False)
+        rows = np.unique(np.random.default_rng(k).integers(0, len(members), 6))
+        fz, hllr = class_inputs(N, K, members[rows], seed + 1)
+        llr[torch.from_numpy(rows).cuda()] = torch.from_numpy(hllr).cuda()
+        n = len(members)
+        uh = torch.empty((n, N), dtype=torch.uint8, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        pe = torch.empty(n, dtype=torch.int64, device="cuda")
+        segs.append((code, llr, uh, it, pe))
+        checks.append((fz, hllr, rows))
+    B.polarbp_decode_segments(segs, 60, ALPHA, 1, 1)
+    torch.cuda.synchronize()
+    for (code, llr, uh, it, pe), (fz, hllr, rows) in zip(segs, checks):
+        sel = torch.from_numpy(rows).cuda()
+        ouh, oit, ope, _ = O.decode_batch(fz, hllr, 60, ALPHA, 1, 1, fp32=True)
+        assert np.array_equal(uh[sel].cpu().numpy(), ouh)
+        assert np.array_equal(it[sel].cpu().numpy(), oit)
+        assert np.array_equal(pe[sel].cpu().numpy(), ope)
