@@ -369,6 +369,93 @@ def run_ours(args):
     return 0
 
 
+MIXED_CLASSES = [(256, 64), (256, 128), (256, 192), (1024, 256), (1024, 512), (1024, 768), (4096, 1024),
+                 (4096, 2048), (4096, 3072)]
+
+
+def run_mixed(args):
+    """Mixed stream: 2^20 codewords, each drawing N from {256, 1024, 4096}, rate from
+    {1/4, 1/2, 3/4} and Eb/N0 from U[1.5, 3.5] dB; G-matrix stop + CSFG freezing, max 60
+    iterations; one persistent launch per code length, captured in a CUDA graph."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    from paper_1505_04979_gb300 import inputs as I
+    build.build()
+    torch.cuda.set_device(0)
+    total = args.batch
+    seed = SEED + 2
+    idx = np.arange(total)
+    cls = I.choice(seed, idx, len(MIXED_CLASSES), which=1)
+    segs, us, info_bits, cpcs = [], [], 0, {}
+    for k, (n_, k_) in enumerate(MIXED_CLASSES):
+        members = idx[cls == k]
+        code = B.polarbp_construct(n_, k_)
+        cpcs[f"{n_},{k_}"] = B.polarbp_autotune(code, MAX_ITER)
+        ebn0 = torch.from_numpy(I.uniform(seed, members, 1.5, 3.5).astype(np.float32)).cuda()
+        u, llr = B.polarbp_awgn_ebn0(code, seed, int(members[0]) if len(members) else 0, ebn0)
+        n = len(members)
+        segs.append((code, llr, torch.empty((n, n_), dtype=torch.uint8, device="cuda"),
+                     torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int64, device="cuda")))
+        us.append(u)
+        info_bits += k_ * n
+    ws = torch.empty(B.polarbp_decode_segments_workspace(), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    B.polarbp_decode_segments(segs, MAX_ITER, ALPHA, 1, 1, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.polarbp_decode_segments(segs, MAX_ITER, ALPHA, 1, 1, workspace=ws, stream=torch.cuda.current_stream())
+    with ClockSampler(0) as clk:
+        ms_graph = timed(g.replay, args.steps)
+    ms_persist = timed(lambda: B.polarbp_decode_segments(segs, MAX_ITER, ALPHA, 1, 1, workspace=ws, stream=stream),
+                       max(3, args.steps // 4))
+
+    def per_class():
+        for code, llr, uh, it, pe in segs:
+            B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, 1, uh, it, pe, stream=stream)
+    ms_plain = timed(per_class, max(3, args.steps // 4))
+    g.replay()
+    torch.cuda.synchronize()
+    per = {}
+    pe_total = 0.0
+    for (n_, k_), (code, llr, uh, it, pe), u in zip(MIXED_CLASSES, segs, us):
+        n = uh.shape[0]
+        errs = int((uh != u).any(dim=1).sum().item())
+        pe_total += float(pe.double().sum().item())
+        per[f"N={n_},K={k_}"] = {"codewords": n, "fer": errs / max(n, 1), "fer_ci95": list(wilson(errs, n)),
+                                 "avg_iters": float(it.double().mean().item()),
+                                 "pe_per_codeword": float(pe.double().mean().item())}
+    line = {"metric": "info Gbit/s/GB300, mixed stream (N in {256,1024,4096}, R in {1/4,1/2,3/4}, Eb/N0 U[1.5,3.5])",
+            "value": info_bits / (ms_graph * 1e-3) / 1e9, "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"mixed stream, {total} codewords per step, G-matrix stop + CSFG freezing, "
+                                   f"max {MAX_ITER} iterations, persistent launches in one CUDA graph",
+                       "codewords_per_block": cpcs},
+            "variants_ms_per_step": {"graph": ms_graph, "persistent_uncaptured": ms_persist,
+                                     "one_block_per_codeword": ms_plain},
+            "roofline": {"bound": "alu", "achieved": pe_total / (ms_graph * 1e-3) / 1e9,
+                         "peak": PEAK_PE_PER_S / 1e9, "unit": "GPE/s",
+                         "frac": pe_total / (ms_graph * 1e-3) / PEAK_PE_PER_S},
+            "classes": per, "clocks": clk.summary(), "gpu_launches": args.steps * len({c[0] for c in MIXED_CLASSES})}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,9 +468,13 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["n1024", "mixed"], default="n1024",
+                    help="n1024: the (1024,512) headline; mixed: the mixed-length stream")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
     return run_ours(args)
 
 

@@ -62,8 +62,10 @@ def _load():
         lib.orc_decode_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, ci, u8p, i32p, i64p,
                                          f64p]
         lib.orc_max_threads.argtypes = []
+        lib.orc_wms_forward.argtypes = [ci, u8p, f32p, ci, f64p, ci, f64p, f64p, f64p]
+        lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, f64p, f64p]
         for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
-                   "orc_decode_batch", "orc_max_threads"):
+                   "orc_decode_batch", "orc_max_threads", "orc_wms_forward", "orc_wms_backward"):
             getattr(lib, fn).restype = ci
         _lib = lib
         return lib
@@ -177,3 +179,37 @@ def decode_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = 
                                   _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double))
     _check(rc, "decode_batch")
     return u_hat, iters, pe, margin
+
+
+def wms_forward(frozen, llr, weights, fp32: bool = False, trace: bool = False):
+    """Weighted min-sum soft outputs (N,) after T iterations; weights [T, m, N/2]."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    N = frozen.shape[0]
+    m = N.bit_length() - 1
+    T = w.shape[0]
+    out = np.zeros(N, np.float64)
+    tl = tr = None
+    if trace:
+        tl = np.zeros((T, m + 1, N), np.float64)
+        tr = np.zeros((T, m + 1, N), np.float64)
+    _check(_load().orc_wms_forward(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), T, _p(w, ctypes.c_double),
+                                   1 if fp32 else 0, _p(out, ctypes.c_double), _p(tl, ctypes.c_double),
+                                   _p(tr, ctypes.c_double)), "wms_forward")
+    return (out, tl, tr) if trace else out
+
+
+def wms_backward(frozen, llr, weights, dout):
+    """(dweights [T, m, N/2], dllr [N]) of sum(dout * out) through wms_forward (FP64)."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    d = np.ascontiguousarray(dout, dtype=np.float64)
+    N = frozen.shape[0]
+    dw = np.zeros_like(w)
+    dl = np.zeros(N, np.float64)
+    _check(_load().orc_wms_backward(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), w.shape[0],
+                                    _p(w, ctypes.c_double), _p(d, ctypes.c_double), _p(dw, ctypes.c_double),
+                                    _p(dl, ctypes.c_double)), "wms_backward")
+    return dw, dl

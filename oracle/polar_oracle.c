@@ -513,3 +513,224 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Weighted min-sum: Eq. (1) with the scaling alpha replaced by one weight    */
+/* per (iteration t, stage s, PE p), T unrolled iterations, no stop and no    */
+/* freezing.  PE p of stage s pairs a and a + h (h = 2^(m-1-s)), p counting   */
+/* the pairs in increasing a:  p = (a >> (m-s)) * h + (a mod h).  Weight      */
+/* (t, s, p) sits at w[(t*m + s)*(N/2) + p].  The soft output of position i   */
+/* is R[m][i] + L[m][i] after the last iteration.                             */
+/*                                                                            */
+/* Gradient.  f_w(x, y) = w h(x, y), h = sign(x) sign(y) min(|x|, |y|):       */
+/*   df/dw = h;  when |x| <= |y| (ties to the first argument) df/dx =         */
+/*   w sign(y), df/dy = 0, else df/dx = 0, df/dy = w sign(x).  Messages that  */
+/*   are +-inf (made from the frozen prior) do not change with any weight or  */
+/*   input: no adjoint flows into or out of them and they add nothing to a    */
+/*   weight's gradient.                                                       */
+/* ------------------------------------------------------------------------ */
+static double wms_f(int fp32, double w, double x, double y)
+{
+    double v = w * sgn(x) * sgn(y) * fmin(fabs(x), fabs(y));
+    return fp32 ? (double)(float)v : v;
+}
+
+static int wms_pair_index(int m, int s, int a)
+{
+    const int h = 1 << (m - 1 - s);
+    return ((a >> (m - s)) * h) + (a & (h - 1));
+}
+
+/* planes_L / planes_R: (T+1) x (m+1) x N; index 0 = before iteration 1 (L), then after each iteration */
+static int wms_run(int N, int m, const uint8_t* frozen, const float* llr, int T, const double* w, int fp32,
+                   double* planes_L, double* planes_R)
+{
+    const size_t P = (size_t)(m + 1) * (size_t)N;
+    double* L = planes_L;
+    double* R = planes_R;
+    for (size_t k = 0; k < P; ++k) L[k] = 0.0, R[k] = 0.0;
+    for (int i = 0; i < N; ++i) L[(size_t)m * N + i] = frozen[i] ? INFINITY : 0.0;
+    for (int t = 1; t <= T; ++t) {
+        double* Lc = planes_L + (size_t)t * P;
+        double* Rc = planes_R + (size_t)t * P;
+        memcpy(Lc, planes_L + (size_t)(t - 1) * P, P * sizeof(double));
+        for (int i = 0; i < N; ++i) Rc[i] = (double)llr[i];
+        for (int s = 0; s < m; ++s) {
+            const int h = 1 << (m - 1 - s);
+            for (int a = 0; a < N; ++a) {
+                if (a & h) continue;
+                const int b = a + h;
+                const double wt = fp32 ? (double)(float)w[((size_t)(t - 1) * m + s) * (N / 2) + wms_pair_index(m, s, a)]
+                                       : w[((size_t)(t - 1) * m + s) * (N / 2) + wms_pair_index(m, s, a)];
+                const double La = Lc[(size_t)(s + 1) * N + a], Lb = Lc[(size_t)(s + 1) * N + b];
+                const double Ra = Rc[(size_t)s * N + a], Rb = Rc[(size_t)s * N + b];
+                double tt = Lb + Rb;
+                if (fp32) tt = (double)(float)tt;
+                const double g = wms_f(fp32, wt, La, Ra);
+                double nLb = Lb + g, nRb = Rb + g;
+                if (fp32) nLb = (double)(float)nLb, nRb = (double)(float)nRb;
+                Lc[(size_t)s * N + a] = wms_f(fp32, wt, La, tt);
+                Lc[(size_t)s * N + b] = nLb;
+                Rc[(size_t)(s + 1) * N + a] = wms_f(fp32, wt, Ra, tt);
+                Rc[(size_t)(s + 1) * N + b] = nRb;
+                if (isnan(tt) || isnan(g)) return ORC_ERR_NAN;
+            }
+        }
+    }
+    (void)L;
+    (void)R;
+    return ORC_OK;
+}
+
+/*
+ * orc_wms_forward -- weighted min-sum decode of one codeword.
+ *   w         T*m*(N/2) weights (layout above), doubles
+ *   out       N soft outputs R[m][i] + L[m][i] after iteration T
+ *   trace_L, trace_R  optional T x (m+1) x N planes after each iteration
+ */
+int orc_wms_forward(int N, const uint8_t* frozen, const float* llr, int T, const double* w, int fp32, double* out,
+                    double* trace_L, double* trace_R)
+{
+    const int m = ilog2_exact(N);
+    if (m < 1 || T < 1 || !frozen || !llr || !w || !out) return ORC_ERR_ARG;
+    const size_t P = (size_t)(m + 1) * (size_t)N;
+    double* pl = (double*)malloc(sizeof(double) * P * (size_t)(T + 1));
+    double* pr = (double*)malloc(sizeof(double) * P * (size_t)(T + 1));
+    if (!pl || !pr) {
+        free(pl);
+        free(pr);
+        return ORC_ERR_NOMEM;
+    }
+    int rc = wms_run(N, m, frozen, llr, T, w, fp32, pl, pr);
+    if (rc == ORC_OK) {
+        const double* Lf = pl + (size_t)T * P;
+        const double* Rf = pr + (size_t)T * P;
+        for (int i = 0; i < N; ++i) {
+            double v = Rf[(size_t)m * N + i] + Lf[(size_t)m * N + i];
+            out[i] = fp32 ? (double)(float)v : v;
+        }
+        if (trace_L) memcpy(trace_L, pl + P, sizeof(double) * P * (size_t)T);
+        if (trace_R) memcpy(trace_R, pr + P, sizeof(double) * P * (size_t)T);
+    }
+    free(pl);
+    free(pr);
+    return rc;
+}
+
+/* derivative of f_w(x, y) with respect to x and y (ties to the first argument) */
+static void wms_df(double w, double x, double y, double* dx, double* dy)
+{
+    if (fabs(x) <= fabs(y)) {
+        *dx = w * sgn(y);
+        *dy = 0.0;
+    } else {
+        *dx = 0.0;
+        *dy = w * sgn(x);
+    }
+}
+
+/* accumulate into an adjoint slot unless the message it belongs to is +-inf */
+static void wms_acc(double* slot, double value, double g)
+{
+    if (!isinf(value)) *slot += g;
+}
+
+/*
+ * orc_wms_backward -- gradient of a loss through orc_wms_forward (FP64).
+ *   dout   N values dLoss/d out[i]
+ *   dw     T*m*(N/2) gradient of the weights (overwritten)
+ *   dllr   N gradient of the channel LLRs (overwritten)
+ */
+int orc_wms_backward(int N, const uint8_t* frozen, const float* llr, int T, const double* w, const double* dout,
+                     double* dw, double* dllr)
+{
+    const int m = ilog2_exact(N);
+    if (m < 1 || T < 1 || !frozen || !llr || !w || !dout || !dw || !dllr) return ORC_ERR_ARG;
+    const size_t P = (size_t)(m + 1) * (size_t)N;
+    double* pl = (double*)malloc(sizeof(double) * P * (size_t)(T + 1));
+    double* pr = (double*)malloc(sizeof(double) * P * (size_t)(T + 1));
+    double* dL = (double*)calloc(P, sizeof(double)); /* adjoint of the L state after the current iteration */
+    double* dLp = (double*)calloc(P, sizeof(double)); /* adjoint of the L state before it */
+    double* dR = (double*)calloc(P, sizeof(double));
+    int rc = (pl && pr && dL && dLp && dR) ? ORC_OK : ORC_ERR_NOMEM;
+    if (rc == ORC_OK) rc = wms_run(N, m, frozen, llr, T, w, 0, pl, pr);
+    if (rc == ORC_OK) {
+        for (size_t k = 0; k < (size_t)T * (size_t)m * (size_t)(N / 2); ++k) dw[k] = 0.0;
+        for (int i = 0; i < N; ++i) dllr[i] = 0.0;
+        /* the soft output R[m] + L[m] of the last iteration; L[m] is the constant prior */
+        for (int i = 0; i < N; ++i) dL[(size_t)m * N + i] = 0.0;
+        for (int t = T; t >= 1; --t) {
+            const double* Lp = pl + (size_t)(t - 1) * P; /* L^{t-1}: PE inputs */
+            const double* Lc = pl + (size_t)t * P;       /* L^t:     PE outputs */
+            const double* Rc = pr + (size_t)t * P;       /* R^t */
+            for (size_t k = 0; k < P; ++k) dR[k] = 0.0, dLp[k] = 0.0;
+            if (t == T)
+                for (int i = 0; i < N; ++i) wms_acc(&dR[(size_t)m * N + i], Rc[(size_t)m * N + i], dout[i]);
+            /* the L state of columns m (prior) and 0 (read by nothing) carries no adjoint */
+            for (int s = m - 1; s >= 0; --s) {
+                const int h = 1 << (m - 1 - s);
+                for (int a = 0; a < N; ++a) {
+                    if (a & h) continue;
+                    const int b = a + h;
+                    const size_t widx = ((size_t)(t - 1) * m + s) * (N / 2) + wms_pair_index(m, s, a);
+                    const double wt = w[widx];
+                    const double La = Lp[(size_t)(s + 1) * N + a], Lb = Lp[(size_t)(s + 1) * N + b];
+                    const double Ra = Rc[(size_t)s * N + a], Rb = Rc[(size_t)s * N + b];
+                    const double tt = Lb + Rb;
+                    const double g = wt * sgn(La) * sgn(Ra) * fmin(fabs(La), fabs(Ra));
+                    /* adjoints of the four outputs (zero for +-inf outputs) */
+                    const double oLa = Lc[(size_t)s * N + a], oLb = Lc[(size_t)s * N + b];
+                    const double oRa = Rc[(size_t)(s + 1) * N + a], oRb = Rc[(size_t)(s + 1) * N + b];
+                    const double gLa = (s >= 1 && !isinf(oLa)) ? dL[(size_t)s * N + a] : 0.0;
+                    const double gLb = (s >= 1 && !isinf(oLb)) ? dL[(size_t)s * N + b] : 0.0;
+                    const double gRa = isinf(oRa) ? 0.0 : dR[(size_t)(s + 1) * N + a];
+                    const double gRb = isinf(oRb) ? 0.0 : dR[(size_t)(s + 1) * N + b];
+                    double dg = 0.0, dt = 0.0, dx, dy;
+                    /* R[s+1][b] = Rb + g ; L[s][b] = Lb + g */
+                    wms_acc(&dR[(size_t)s * N + b], Rb, gRb);
+                    if (!isinf(g)) dg += gRb;
+                    wms_acc(&dLp[(size_t)(s + 1) * N + b], Lb, gLb);
+                    if (!isinf(oLb)) dg += gLb;
+                    /* R[s+1][a] = f(Ra, t) */
+                    if (!isinf(oRa) && gRa != 0.0) {
+                        wms_df(wt, Ra, tt, &dx, &dy);
+                        wms_acc(&dR[(size_t)s * N + a], Ra, gRa * dx);
+                        if (!isinf(tt)) dt += gRa * dy;
+                        dw[widx] += gRa * sgn(Ra) * sgn(tt) * fmin(fabs(Ra), fabs(tt));
+                    }
+                    /* L[s][a] = f(La, t) */
+                    if (!isinf(oLa) && gLa != 0.0) {
+                        wms_df(wt, La, tt, &dx, &dy);
+                        wms_acc(&dLp[(size_t)(s + 1) * N + a], La, gLa * dx);
+                        if (!isinf(tt)) dt += gLa * dy;
+                        dw[widx] += gLa * sgn(La) * sgn(tt) * fmin(fabs(La), fabs(tt));
+                    }
+                    /* g = f(La, Ra) */
+                    if (!isinf(g) && dg != 0.0) {
+                        wms_df(wt, La, Ra, &dx, &dy);
+                        wms_acc(&dLp[(size_t)(s + 1) * N + a], La, dg * dx);
+                        wms_acc(&dR[(size_t)s * N + a], Ra, dg * dy);
+                        dw[widx] += dg * sgn(La) * sgn(Ra) * fmin(fabs(La), fabs(Ra));
+                    }
+                    /* t = Lb + Rb */
+                    if (!isinf(tt)) {
+                        wms_acc(&dLp[(size_t)(s + 1) * N + b], Lb, dt);
+                        wms_acc(&dR[(size_t)s * N + b], Rb, dt);
+                    }
+                }
+            }
+            for (int i = 0; i < N; ++i) dllr[i] += dR[i];
+            /* the L state before iteration t: columns 1..m-1 carry over; iteration 1 reads the start state */
+            double* tmp = dL;
+            dL = dLp;
+            dLp = tmp;
+            for (int i = 0; i < N; ++i) dL[(size_t)m * N + i] = 0.0, dL[i] = 0.0;
+        }
+    }
+    free(pl);
+    free(pr);
+    free(dL);
+    free(dLp);
+    free(dR);
+    return rc;
+}
