@@ -272,6 +272,37 @@ int polarbp_awgn_ebn0(const polarbp_code* code, uint64_t seed, uint64_t first_co
                       const float* ebn0_db, uint8_t* u, float* llr, void* stream);
 
 /*
+ * Weighted min-sum (trainable scalings).  Eq. (1) with alpha replaced by one
+ * weight per (iteration t, stage s, PE p), `iterations` unrolled iterations
+ * with the schedule of polarbp_decode, no stop and no freezing.  PE p of stage
+ * s pairs positions a and a + 2^(m-1-s), p = (a >> (m-s)) 2^(m-1-s) +
+ * (a mod 2^(m-1-s)).  Supported N: 2 .. 1024.
+ *   weights   device [iterations][m][N/2] float, weight (t, s, p) at (t m + s) N/2 + p.
+ *   out       device [batch][N] soft outputs R[m] + L[m] after the last
+ *             iteration (+inf on frozen positions: the prior).
+ *   workspace device buffer of polarbp_wms_workspace(code, batch, iterations)
+ *             bytes: the forward writes its per-iteration checkpoints there and
+ *             the backward of the same batch reads them; keep it unchanged
+ *             between the two.
+ */
+size_t polarbp_wms_workspace(const polarbp_code* code, int batch, int iterations);
+int polarbp_wms_forward(const polarbp_code* code, const float* llr, int batch, int iterations, const float* weights,
+                        float* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * polarbp_wms_backward -- gradients of a loss through polarbp_wms_forward.
+ *   dout      device [batch][N]: dLoss/d out (entries at frozen positions are ignored).
+ *   dweights  device [iterations][m][N/2]: dLoss/d weights, summed over the batch
+ *             in codeword order (overwritten).
+ *   dllr      device [batch][N]: dLoss/d llr (overwritten).
+ * min is differentiated towards its smaller argument (ties: the first), sign
+ * as a constant; +-inf messages (built from the frozen prior) are constants.
+ */
+int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, int iterations, const float* weights,
+                         const float* dout, float* dweights, float* dllr, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/*
  * polarbp_get_status -- read and clear the handle's device status word.  Waits
  * for `stream`.  Returns POLARBP_ERR_NONFINITE when a decode since the last
  * call saw a non-finite LLR, else POLARBP_OK (or POLARBP_ERR_CUDA).

@@ -345,6 +345,14 @@ int noalloc_scratch_address(void** out)
 
 }  // namespace
 
+// accessors shared with the other translation units of the library
+namespace polarbp_internal {
+const uint32_t* frozen_words(const polarbp_code* c) { return c->d_frozen; }
+int fail(int code, const std::string& msg) { return ::fail(code, msg); }
+int cuda_fail(cudaError_t e, const char* what) { return ::cuda_fail(e, what); }
+int check_device(const polarbp_code* c) { return ::check_device(c); }
+}  // namespace polarbp_internal
+
 extern "C" {
 
 int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polarbp_code** out)

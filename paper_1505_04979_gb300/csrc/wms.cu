@@ -1,0 +1,333 @@
+// wms.cu -- weighted min-sum BP forward / adjoint for learning per-PE scalings.
+//
+// The decoder is Eq. (1) (Sec. II-A) with the min-sum scaling alpha replaced by
+// one weight per (iteration t, stage s, PE p), T unrolled iterations, no stop
+// and no freezing.  PE p of stage s pairs a and a + h (h = 2^(m-1-s)) with
+// p = (a >> (m-s)) h + (a mod h); weight (t, s, p) sits at
+// w[(t m + s) N/2 + p].  The soft output of position i is R[m][i] + L[m][i]
+// after the last iteration (+inf on frozen positions, the prior).
+//
+// Gradient of f_w(x, y) = w h(x, y), h = sign(x) sign(y) min(|x|, |y|):
+// df/dw = h; when |x| <= |y| (ties to the first argument) df/dx = w sign(y),
+// df/dy = 0, else df/dx = 0, df/dy = w sign(x).  Messages that are +-inf
+// (built from the frozen prior) do not change with any weight or input: no
+// adjoint flows into or out of them and they add nothing to a weight's
+// gradient.
+//
+// One block of N/2 threads (at least 32) per codeword, one PE per thread per
+// stage, all message planes in shared memory; the forward checkpoints L and R
+// after every iteration to the caller's workspace, the adjoint reads them back
+// in reverse order and writes one gradient partial per codeword, which a
+// second kernel sums over the batch in a fixed order.
+#include <cmath>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "polarbp.h"
+
+namespace {
+
+struct WmsShape {
+    int N, m, T;
+    size_t plane;  // (m+1) N
+};
+
+__device__ __forceinline__ float wsgn(float v) { return (float)((v > 0.f) - (v < 0.f)); }
+
+// w * sign(x) sign(y) min(|x|, |y|): exact magnitude, one rounding for the product
+__device__ __forceinline__ float wmin(float w, float x, float y)
+{
+    const float mag = __fmul_rn(w, fminf(fabsf(x), fabsf(y)));
+    const uint32_t s = (__float_as_uint(x) ^ __float_as_uint(y)) & 0x80000000u;
+    return __uint_as_float(__float_as_uint(mag) | s);
+}
+
+__device__ __forceinline__ float hval(float x, float y)
+{
+    return wsgn(x) * wsgn(y) * fminf(fabsf(x), fabsf(y));
+}
+
+__device__ __forceinline__ int pair_a(int m, int s, int p)
+{
+    const int h = 1 << (m - 1 - s);
+    return (p / h) * 2 * h + (p % h);
+}
+
+// checkpoints: [batch][T][2][(m+1)][N]: L after iteration t, then R after iteration t
+__global__ void wms_forward_kernel(const float* __restrict__ llr, const uint32_t* __restrict__ frozen_words,
+                                   const float* __restrict__ w, int N, int m, int T, float* __restrict__ out,
+                                   float* __restrict__ ckpt)
+{
+    extern __shared__ float sh[];
+    float* L = sh;                        // (m+1) N
+    float* R = sh + (size_t)(m + 1) * N;  // (m+1) N
+    const long long cw = blockIdx.x;
+    const int plane = (m + 1) * N;
+    for (int k = threadIdx.x; k < plane; k += blockDim.x) {
+        const int c = k / N, i = k % N;
+        L[k] = (c == m) ? (((frozen_words[i >> 5] >> (i & 31)) & 1u) ? INFINITY : 0.f) : 0.f;
+        R[k] = 0.f;
+    }
+    __syncthreads();
+    const int p = threadIdx.x;
+    for (int t = 0; t < T; ++t) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) R[i] = llr[cw * N + i];
+        __syncthreads();
+        for (int s = 0; s < m; ++s) {
+            if (p < N / 2) {
+                const int h = 1 << (m - 1 - s);
+                const int a = pair_a(m, s, p), b = a + h;
+                const float wt = __ldg(w + ((size_t)t * m + s) * (N / 2) + p);
+                const float La = L[(s + 1) * N + a], Lb = L[(s + 1) * N + b];
+                const float Ra = R[s * N + a], Rb = R[s * N + b];
+                const float tt = __fadd_rn(Lb, Rb);
+                const float g = wmin(wt, La, Ra);
+                L[s * N + a] = wmin(wt, La, tt);
+                L[s * N + b] = __fadd_rn(Lb, g);
+                R[(s + 1) * N + a] = wmin(wt, Ra, tt);
+                R[(s + 1) * N + b] = __fadd_rn(Rb, g);
+            }
+            __syncthreads();
+        }
+        float* dst = ckpt + ((size_t)cw * T + t) * 2 * plane;
+        for (int k = threadIdx.x; k < plane; k += blockDim.x) {
+            dst[k] = L[k];
+            dst[plane + k] = R[k];
+        }
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) out[cw * N + i] = __fadd_rn(R[m * N + i], L[m * N + i]);
+}
+
+__device__ __forceinline__ void acc(float* slot, float value, float g)
+{
+    if (!isinf(value)) *slot += g;
+}
+
+// partials: [batch][T m N/2]
+__global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_t* __restrict__ frozen_words,
+                                    const float* __restrict__ w, int N, int m, int T, const float* __restrict__ ckpt,
+                                    const float* __restrict__ dout, float* __restrict__ partial,
+                                    float* __restrict__ dllr)
+{
+    extern __shared__ float sh[];
+    const int plane = (m + 1) * N;
+    float* dL = sh;            // adjoint of the L state after the current iteration
+    float* dLp = sh + plane;   // adjoint of the L state before it
+    float* dR = sh + 2 * plane;
+    float* L0 = sh + 3 * plane;  // the L state before iteration 1
+    const long long cw = blockIdx.x;
+    for (int k = threadIdx.x; k < plane; k += blockDim.x) {
+        const int c = k / N, i = k % N;
+        dL[k] = 0.f;
+        L0[k] = (c == m) ? (((frozen_words[i >> 5] >> (i & 31)) & 1u) ? INFINITY : 0.f) : 0.f;
+    }
+    float dl_acc[4] = {0.f, 0.f, 0.f, 0.f};  // dllr of positions threadIdx.x + j blockDim.x (N <= 4 blockDim.x)
+    __syncthreads();
+    const int p = threadIdx.x;
+    const size_t W = (size_t)T * m * (N / 2);
+    for (int t = T - 1; t >= 0; --t) {
+        const float* Lc = ckpt + ((size_t)cw * T + t) * 2 * plane;                            // L^t
+        const float* Rc = Lc + plane;                                                         // R^t
+        const float* Lp = t > 0 ? ckpt + ((size_t)cw * T + (t - 1)) * 2 * plane : L0;         // L^{t-1}
+        for (int k = threadIdx.x; k < plane; k += blockDim.x) {
+            dR[k] = 0.f;
+            dLp[k] = 0.f;
+        }
+        __syncthreads();
+        if (t == T - 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) acc(&dR[m * N + i], Rc[m * N + i], dout[cw * N + i]);
+        }
+        __syncthreads();
+        for (int s = m - 1; s >= 0; --s) {
+            if (p < N / 2) {
+                const int h = 1 << (m - 1 - s);
+                const int a = pair_a(m, s, p), b = a + h;
+                const size_t widx = ((size_t)t * m + s) * (N / 2) + p;
+                const float wt = __ldg(w + widx);
+                const float La = Lp[(s + 1) * N + a], Lb = Lp[(s + 1) * N + b];
+                const float Ra = Rc[s * N + a], Rb = Rc[s * N + b];
+                const float tt = __fadd_rn(Lb, Rb);
+                const float g = wmin(wt, La, Ra);
+                const float oLa = Lc[s * N + a], oLb = Lc[s * N + b];
+                const float oRa = Rc[(s + 1) * N + a], oRb = Rc[(s + 1) * N + b];
+                const float gLa = (s >= 1 && !isinf(oLa)) ? dL[s * N + a] : 0.f;
+                const float gLb = (s >= 1 && !isinf(oLb)) ? dL[s * N + b] : 0.f;
+                const float gRa = isinf(oRa) ? 0.f : dR[(s + 1) * N + a];
+                const float gRb = isinf(oRb) ? 0.f : dR[(s + 1) * N + b];
+                float dg = 0.f, dt = 0.f, dw = 0.f;
+                acc(&dR[s * N + b], Rb, gRb);
+                if (!isinf(g)) dg += gRb;
+                acc(&dLp[(s + 1) * N + b], Lb, gLb);
+                if (!isinf(oLb)) dg += gLb;
+                if (!isinf(oRa) && gRa != 0.f) {
+                    if (fabsf(Ra) <= fabsf(tt)) acc(&dR[s * N + a], Ra, gRa * wt * wsgn(tt));
+                    else if (!isinf(tt)) dt += gRa * wt * wsgn(Ra);
+                    dw += gRa * hval(Ra, tt);
+                }
+                if (!isinf(oLa) && gLa != 0.f) {
+                    if (fabsf(La) <= fabsf(tt)) acc(&dLp[(s + 1) * N + a], La, gLa * wt * wsgn(tt));
+                    else if (!isinf(tt)) dt += gLa * wt * wsgn(La);
+                    dw += gLa * hval(La, tt);
+                }
+                if (!isinf(g) && dg != 0.f) {
+                    if (fabsf(La) <= fabsf(Ra)) acc(&dLp[(s + 1) * N + a], La, dg * wt * wsgn(Ra));
+                    else acc(&dR[s * N + a], Ra, dg * wt * wsgn(La));
+                    dw += dg * hval(La, Ra);
+                }
+                if (!isinf(tt)) {
+                    acc(&dLp[(s + 1) * N + b], Lb, dt);
+                    acc(&dR[s * N + b], Rb, dt);
+                }
+                partial[(size_t)cw * W + widx] = dw;
+            }
+            __syncthreads();
+        }
+        for (int j = 0; j < 4; ++j) {
+            const int i = threadIdx.x + j * blockDim.x;
+            if (i < N) dl_acc[j] += dR[i];
+        }
+        __syncthreads();
+        float* tmp = dL;
+        dL = dLp;
+        dLp = tmp;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            dL[m * N + i] = 0.f;
+            dL[i] = 0.f;
+        }
+        __syncthreads();
+    }
+    for (int j = 0; j < 4; ++j) {
+        const int i = threadIdx.x + j * blockDim.x;
+        if (i < N) dllr[cw * N + i] = dl_acc[j];
+    }
+}
+
+// dw[k] = sum over codewords of partial[cw][k], in codeword order
+__global__ void wms_reduce_kernel(const float* __restrict__ partial, int batch, size_t W, float* __restrict__ dw)
+{
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= W) return;
+    float acc_v = 0.f;
+    for (int c = 0; c < batch; ++c) acc_v += partial[(size_t)c * W + k];
+    dw[k] = acc_v;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side (declared in include/polarbp.h)
+// ---------------------------------------------------------------------------
+struct polarbp_code;  // opaque here: the accessors below come from polarbp_api.cu
+extern "C" int polarbp_code_info(const polarbp_code* code, int* N, int* K, int* m);
+namespace polarbp_internal {
+const uint32_t* frozen_words(const polarbp_code* c);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+int check_device(const polarbp_code* c);
+}  // namespace polarbp_internal
+
+namespace {
+struct WmsLayout {
+    size_t ckpt, partial, total;
+};
+WmsLayout wms_layout(int N, int m, int batch, int T)
+{
+    WmsLayout l;
+    l.ckpt = 0;
+    l.partial = align256((size_t)batch * T * 2 * (m + 1) * N * sizeof(float));
+    l.total = align256(l.partial + (size_t)batch * T * m * (N / 2) * sizeof(float));
+    return l;
+}
+
+int wms_args(const polarbp_code* c, int batch, int T, int* N, int* m)
+{
+    using namespace polarbp_internal;
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    if (T < 1) return fail(POLARBP_ERR_ARG, "iterations must be >= 1");
+    polarbp_code_info(c, N, nullptr, m);
+    if (*m > 10) return fail(POLARBP_ERR_UNSUPPORTED, "weighted min-sum supports N <= 1024");
+    return POLARBP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t polarbp_wms_workspace(const polarbp_code* code, int batch, int iterations)
+{
+    int N = 0, m = 0;
+    if (!code || batch < 0 || iterations < 1) return 0;
+    polarbp_code_info(code, &N, nullptr, &m);
+    return wms_layout(N, m, batch, iterations).total;
+}
+
+int polarbp_wms_forward(const polarbp_code* code, const float* llr, int batch, int iterations, const float* weights,
+                        float* out, void* workspace, size_t workspace_bytes, void* stream)
+{
+    using namespace polarbp_internal;
+    int N = 0, m = 0;
+    int rc = wms_args(code, batch, iterations, &N, &m);
+    if (rc != POLARBP_OK) return rc;
+    if (batch == 0) return POLARBP_OK;
+    if (!llr || !weights || !out) return fail(POLARBP_ERR_ARG, "llr, weights and out must be device pointers");
+    const WmsLayout l = wms_layout(N, m, batch, iterations);
+    if (!workspace || workspace_bytes < l.total) return fail(POLARBP_ERR_ARG, "workspace too small");
+    rc = check_device(code);
+    if (rc != POLARBP_OK) return rc;
+    const int threads = N / 2 < 32 ? 32 : N / 2;
+    const size_t smem = 2 * (size_t)(m + 1) * N * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(wms_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "wms forward attribute");
+    }
+    float* ckpt = reinterpret_cast<float*>(static_cast<char*>(workspace) + l.ckpt);
+    wms_forward_kernel<<<batch, threads, smem, static_cast<cudaStream_t>(stream)>>>(
+        llr, frozen_words(code), weights, N, m, iterations, out, ckpt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wms forward launch");
+    return POLARBP_OK;
+}
+
+int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, int iterations, const float* weights,
+                         const float* dout, float* dweights, float* dllr, void* workspace, size_t workspace_bytes,
+                         void* stream)
+{
+    using namespace polarbp_internal;
+    int N = 0, m = 0;
+    int rc = wms_args(code, batch, iterations, &N, &m);
+    if (rc != POLARBP_OK) return rc;
+    if (!weights || !dweights) return fail(POLARBP_ERR_ARG, "weights and dweights must be device pointers");
+    const size_t W = (size_t)iterations * m * (N / 2);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (batch == 0) {
+        cudaError_t e = cudaMemsetAsync(dweights, 0, W * sizeof(float), s);
+        return e == cudaSuccess ? POLARBP_OK : cuda_fail(e, "wms backward");
+    }
+    if (!llr || !dout || !dllr) return fail(POLARBP_ERR_ARG, "llr, dout and dllr must be device pointers");
+    const WmsLayout l = wms_layout(N, m, batch, iterations);
+    if (!workspace || workspace_bytes < l.total) return fail(POLARBP_ERR_ARG, "workspace too small");
+    rc = check_device(code);
+    if (rc != POLARBP_OK) return rc;
+    const int threads = N / 2 < 32 ? 32 : N / 2;
+    const size_t smem = 4 * (size_t)(m + 1) * N * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(wms_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "wms backward attribute");
+    }
+    const float* ckpt = reinterpret_cast<const float*>(static_cast<const char*>(workspace) + l.ckpt);
+    float* partial = reinterpret_cast<float*>(static_cast<char*>(workspace) + l.partial);
+    wms_backward_kernel<<<batch, threads, smem, s>>>(llr, frozen_words(code), weights, N, m, iterations, ckpt, dout,
+                                                     partial, dllr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wms backward launch");
+    wms_reduce_kernel<<<(unsigned)((W + 255) / 256), 256, 0, s>>>(partial, batch, W, dweights);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wms reduce launch");
+    return POLARBP_OK;
+}
+
+}  // extern "C"
