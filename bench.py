@@ -456,6 +456,103 @@ def run_mixed(args):
     return 0
 
 
+def run_wms(args):
+    """Learned weighted min-sum: per-(iteration, stage, PE) weights, 10 unrolled iterations,
+    N in {128, 256}, K = N/2, training batches of 4096 codewords at Eb/N0 ~ U[1, 4] dB, BCE on
+    the information positions, Adam; then FER of the learned weights against constant 0.9375."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    from paper_1505_04979_gb300 import inputs as I
+    build.build()
+    torch.cuda.set_device(0)
+    T, batch = 10, 4096
+    hbm = 6794.8e9
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] * 1e9
+    except (OSError, KeyError, ValueError):
+        pass
+    results = {}
+    stream = torch.cuda.current_stream()
+    for N in (128, 256):
+        K = N // 2
+        m = N.bit_length() - 1
+        code = B.polarbp_construct(N, K)
+        info = torch.from_numpy(np.nonzero(code.frozen_mask() == 0)[0]).cuda()
+        w = torch.full((T, m, N // 2), ALPHA, dtype=torch.float32, device="cuda", requires_grad=True)
+        opt = torch.optim.Adam([w], lr=args.wms_lr)
+        ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
+        losses, fwd_ms, bwd_ms = [], 0.0, 0.0
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        for step in range(args.wms_steps):
+            ebn0 = torch.from_numpy(I.uniform(SEED + 5, np.arange(step * batch, (step + 1) * batch), 1.0, 4.0)
+                                    .astype(np.float32)).cuda()
+            u, llr = B.polarbp_awgn_ebn0(code, SEED + 5, step * batch, ebn0)
+            target = u[:, info].float()
+            opt.zero_grad()
+            e0.record(stream)
+            out = B.polarbp_wms_forward(code, llr, w.detach(), ws)
+            e1.record(stream)
+            x = (-out[:, info]).detach().requires_grad_(True)
+            loss = torch.nn.functional.binary_cross_entropy_with_logits(x, target)
+            loss.backward()
+            dout = torch.zeros((batch, N), dtype=torch.float32, device="cuda")
+            dout[:, info] = -x.grad
+            dw, _ = B.polarbp_wms_backward(code, llr, w.detach(), dout, ws)
+            e2.record(stream)
+            w.grad = dw
+            opt.step()
+            torch.cuda.synchronize()
+            if step >= 3:
+                fwd_ms += e0.elapsed_time(e1)
+                bwd_ms += e1.elapsed_time(e2)
+            losses.append(float(loss.detach()))
+        timed = max(1, args.wms_steps - 3)
+        fwd_ms /= timed
+        bwd_ms /= timed
+        plane = (m + 1) * N * 4
+        fwd_bytes = batch * (4 * N + 4 * N + 2 * T * plane)
+        bwd_bytes = batch * (2 * T * plane + 4 * N * 3 + T * m * (N // 2) * 4)
+        fer = {}
+        with torch.no_grad():
+            for eb in (2.0, 3.0, 4.0):
+                n_eval, errs_l, errs_c = 0, 0, 0
+                wc = torch.full_like(w, ALPHA)
+                for chunk in range(args.wms_eval // batch):
+                    first = (1 << 30) + chunk * batch
+                    u, llr = B.polarbp_awgn(code, SEED + 6, first, batch, eb)
+                    for weights, key in ((w.detach(), "learned"), (wc, "constant")):
+                        out = B.polarbp_wms_forward(code, llr, weights, ws)
+                        uh = (out[:, info] < 0).to(torch.uint8)
+                        e = int((uh != u[:, info]).any(dim=1).sum().item())
+                        if key == "learned":
+                            errs_l += e
+                        else:
+                            errs_c += e
+                    n_eval += batch
+                fer[f"{eb} dB"] = {"codewords": n_eval, "learned": errs_l / n_eval,
+                                   "learned_ci95": list(wilson(errs_l, n_eval)),
+                                   "constant_0.9375": errs_c / n_eval,
+                                   "constant_ci95": list(wilson(errs_c, n_eval))}
+        results[f"N={N}"] = {
+            "train_steps": args.wms_steps, "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:])),
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "train_codewords_per_s": batch / ((fwd_ms + bwd_ms) * 1e-3),
+            "forward_GBps": fwd_bytes / (fwd_ms * 1e-3) / 1e9, "backward_GBps": bwd_bytes / (bwd_ms * 1e-3) / 1e9,
+            "forward_hbm_frac": fwd_bytes / (fwd_ms * 1e-3) / hbm, "backward_hbm_frac": bwd_bytes / (bwd_ms * 1e-3) / hbm,
+            "fer": fer}
+    line = {"metric": "weighted min-sum training: codewords/s (forward + adjoint), FER learned vs constant",
+            "value": results["N=256"]["train_codewords_per_s"], "unit": "codewords/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"weighted min-sum, T={T}, batch {batch}, Eb/N0 U[1,4] dB, Adam lr {args.wms_lr}"},
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm / 1e9,
+                         "achieved": results["N=256"]["backward_GBps"],
+                         "frac": results["N=256"]["backward_hbm_frac"], "kernel": "wms_backward_kernel"},
+            "results": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,13 +565,18 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["n1024", "mixed"], default="n1024",
-                    help="n1024: the (1024,512) headline; mixed: the mixed-length stream")
+    ap.add_argument("--workload", choices=["n1024", "mixed", "wms"], default="n1024",
+                    help="n1024: the (1024,512) headline; mixed: the mixed-length stream; wms: learned weights")
+    ap.add_argument("--wms-steps", type=int, default=300)
+    ap.add_argument("--wms-lr", type=float, default=0.005)
+    ap.add_argument("--wms-eval", type=int, default=1 << 17)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "mixed":
         return run_mixed(args)
+    if args.workload == "wms":
+        return run_wms(args)
     return run_ours(args)
 
 
