@@ -456,6 +456,63 @@ def run_mixed(args):
     return 0
 
 
+def run_long(args):
+    """Long codes: N in {8192, 16384, 32768}, K = N/2, Eb/N0 in {2.0, 2.5, 3.0} dB, 10^5
+    codewords per point (device generator), G-matrix stop + CSFG freezing, at most 100
+    iterations; one codeword per thread-block cluster of N/4096 blocks."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    n_cw = args.long_codewords
+    stream = torch.cuda.current_stream()
+    points, tot_bits, tot_ms, tot_pe = {}, 0.0, 0.0, 0.0
+    with ClockSampler(0) as clk:
+        for N in (8192, 16384, 32768):
+            K = N // 2
+            code = B.polarbp_construct(N, K)
+            for eb in (2.0, 2.5, 3.0):
+                u, llr = B.polarbp_awgn(code, SEED + 3, 0, n_cw, eb)
+                uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
+                it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
+                pe = torch.empty(n_cw, dtype=torch.int64, device="cuda")
+                for _ in range(args.warmup):
+                    B.polarbp_decode(code, llr, 100, ALPHA, 1, 1, uh, it, pe, stream=stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    B.polarbp_decode(code, llr, 100, ALPHA, 1, 1, uh, it, pe, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                errs = int((uh != u).any(dim=1).sum().item())
+                pe_sum = float(pe.double().sum().item())
+                points[f"N={N},{eb}dB"] = {
+                    "codewords": n_cw, "ms": ms, "info_gbps": K * n_cw / (ms * 1e-3) / 1e9,
+                    "codewords_per_s": n_cw / (ms * 1e-3), "fer": errs / n_cw, "fer_ci95": list(wilson(errs, n_cw)),
+                    "avg_iters": float(it.double().mean().item()), "pe_per_codeword": pe_sum / n_cw,
+                    "gpe_per_s": pe_sum / (ms * 1e-3) / 1e9}
+                tot_bits += K * n_cw
+                tot_ms += ms
+                tot_pe += pe_sum
+                del u, llr, uh, it, pe
+                torch.cuda.empty_cache()
+    line = {"metric": "info Gbit/s/GB300, long codes N in {8192,16384,32768}, Eb/N0 {2.0,2.5,3.0} dB",
+            "value": tot_bits / (tot_ms * 1e-3) / 1e9, "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"long codes, K=N/2, {n_cw} codewords per point, 9 points per step, "
+                                   "G-matrix stop + CSFG freezing, max 100 iterations, thread-block clusters",
+                       "l2": "inputs larger than L2 (13 GB of LLRs at N=32768)"},
+            "roofline": {"bound": "alu", "achieved": tot_pe / (tot_ms * 1e-3) / 1e9, "peak": PEAK_PE_PER_S / 1e9,
+                         "unit": "GPE/s", "frac": tot_pe / (tot_ms * 1e-3) / PEAK_PE_PER_S},
+            "points": points, "clocks": clk.summary(), "gpu_launches": 9 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_wms(args):
     """Learned weighted min-sum: per-(iteration, stage, PE) weights, 10 unrolled iterations,
     N in {128, 256}, K = N/2, training batches of 4096 codewords at Eb/N0 ~ U[1, 4] dB, BCE on
@@ -565,8 +622,10 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["n1024", "mixed", "wms"], default="n1024",
-                    help="n1024: the (1024,512) headline; mixed: the mixed-length stream; wms: learned weights")
+    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms"], default="n1024",
+                    help="n1024: the (1024,512) headline; mixed: the mixed-length stream; long: N = 8192..32768 "
+                         "on thread-block clusters; wms: learned weights")
+    ap.add_argument("--long-codewords", type=int, default=100000)
     ap.add_argument("--wms-steps", type=int, default=300)
     ap.add_argument("--wms-lr", type=float, default=0.005)
     ap.add_argument("--wms-eval", type=int, default=1 << 17)
@@ -577,6 +636,8 @@ def main():
         return run_mixed(args)
     if args.workload == "wms":
         return run_wms(args)
+    if args.workload == "long":
+        return run_long(args)
     return run_ours(args)
 
 

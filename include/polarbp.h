@@ -120,7 +120,10 @@ int polarbp_encode(const polarbp_code* code, const uint8_t* u, uint8_t* x, int b
  *   iterations   device [batch] int32 iterations run, or NULL.
  *   pe_updates   device [batch] int64 PE updates executed, counted as in
  *                Sec. IV (each active PE of each iteration counts once), or NULL.
- * Supported N: 2..4096 (one codeword per thread block, messages on chip).
+ * Supported N: 2..32768.  Up to 4096 one thread block decodes a codeword with
+ * every message on chip; 8192, 16384 and 32768 run one codeword per cluster of
+ * 2, 4 or 8 thread blocks, each holding 4096 positions of every message column
+ * and reading its partners' columns through distributed shared memory.
  * A NaN or infinite LLR is recorded in the handle's status word; read it with
  * polarbp_get_status.  Errors: POLARBP_ERR_ARG, POLARBP_ERR_UNSUPPORTED,
  * POLARBP_ERR_CUDA (launch failure).
@@ -139,7 +142,7 @@ int polarbp_decode(const polarbp_code* code, const float* llr, int batch, int ma
  *                     Iterations after the stop are left untouched.
  *   trace_P           [batch][max_iter] int32: length of the covered prefix of
  *                     source positions at the end of each iteration.
- * Slow (every message goes to global memory); N <= 4096.
+ * Slow (every message goes to global memory); N <= 32768.
  */
 int polarbp_decode_trace(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
                          int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,

@@ -188,8 +188,10 @@ struct Smem {
     uint32_t* Xf;   // [(M+1)][NW] hard decisions of the latest feedback event per column
     int* ctl;
     uint8_t* hd;    // [(M+1)][HDS] hard-decision snapshots (one byte per thread)
+    float* L0;      // column 0 of a sweep that is the lower part of a larger code (else unused)
     __device__ __forceinline__ explicit Smem(unsigned char* base)
     {
+        L0 = nullptr;
         using L = SmemLayout<M>;
         Lb = reinterpret_cast<float*>(base + L::off_Lb);
         Rx = reinterpret_cast<float*>(base + L::off_Rx);
@@ -625,13 +627,21 @@ __device__ __forceinline__ float load_L(Regs<M>& rg, Smem<M>& sm, int e, int pb)
 // Store L of column C; with keep set (the PE lies in a covered CSFG) the old
 // value, possibly a +-inf freeze feedback, stays.  Covered PEs are still
 // evaluated: their R outputs are never read again, and evaluating them keeps
-// the sweep free of branches.
-template <int M, int PH, int C>
+// the sweep free of branches.  Column 0 is not stored unless the sweep is the
+// lower part of a larger code (XC > 0 upper stages run elsewhere): then it is
+// the column those stages read, kept in natural order in sm.L0 (phase 0 maps
+// element e of thread t to position e * T + t, passed here as pb = t).
+template <int M, int PH, int C, int XC = 0>
 __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb, float v, bool keep)
 {
     using G = Geo<M>;
     if constexpr (C == 0) {
-        (void)rg; (void)sm; (void)e; (void)pb; (void)v; (void)keep;
+        if constexpr (XC > 0) {
+            static_assert(PH == 0 && G::NP > 1, "column 0 is written in phase 0");
+            if (!keep) sm.L0[e * G::T + pb] = v;
+        } else {
+            (void)rg; (void)sm; (void)e; (void)pb; (void)v; (void)keep;
+        }
     } else if constexpr (G::is_boundary(C)) {
         constexpr int SH = G::padsh(G::bslot(C));
         if (!keep) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
@@ -640,7 +650,11 @@ __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb,
     }
 }
 
-template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE>
+// Stage s of phase PH.  With XC > 0 the sweep is the lower M stages of a code
+// of M + XC stages (stage s here is stage s + XC there): P0 is then the covered
+// prefix within this part, stage 0 may be covered, its L column is stored, the
+// channel-side decisions are taken elsewhere and trace columns are N << XC apart.
+template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE, int XC = 0>
 __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha, const CwIO& a,
                                           long long trace_base)
 {
@@ -650,18 +664,19 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     constexpr int b = M - 1 - s;
     constexpr int k = b - G::lo(PH);
     constexpr bool snap = FREEZE || (GSTOP && s == M - 1);
-    const int thr = (s == 0 || !FREEZE) ? 0 : ((P0 >> (M - s)) << (M - s));
+    constexpr long long TSTRIDE = (long long)N << XC;
+    const int thr = (s + XC == 0 || !FREEZE) ? 0 : ((P0 >> (M - s)) << (M - s));
     uint32_t xbyte = 0;  // stage 0: decisions on R[0] + L[0] (G-matrix stop)
     // padded bases for the boundary columns read (s+1) and written (s) here
     const int pb_in = G::is_boundary(s + 1) ? padded_base<M, PH, G::padsh(G::bslot(s + 1))>(tid) : 0;
-    const int pb_out = G::is_boundary(s) ? padded_base<M, PH, G::padsh(G::bslot(s))>(tid) : 0;
+    const int pb_out = G::is_boundary(s) ? padded_base<M, PH, G::padsh(G::bslot(s))>(tid) : (s == 0 ? tid : 0);
 #pragma unroll
     for (int e = 0; e < EL; ++e) {
         if (e & (1 << k)) continue;
         const int e2 = e | (1 << k);
         const int ia = elem_index<M, PH>(tid, e);
         const int ib = ia + (1 << b);
-        const bool covered = FREEZE && s > 0 && ia < thr;  // PE inside a covered CSFG
+        const bool covered = FREEZE && s + XC > 0 && ia < thr;  // PE inside a covered CSFG
         const float La = load_L<M, PH, s + 1>(rg, sm, e, pb_in);
         const float Lb = load_L<M, PH, s + 1>(rg, sm, e2, pb_in);
         const float Ra = rg.R[e];
@@ -672,20 +687,20 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         const float nLb = __fadd_rn(Lb, g);
         const float nRa = fms(Ra, t, alpha);
         const float nRb = __fadd_rn(Rb, g);
-        store_L<M, PH, s>(rg, sm, e, pb_out, nLa, covered);
-        store_L<M, PH, s>(rg, sm, e2, pb_out, nLb, covered);
-        if constexpr (s == 0 && GSTOP) {
+        store_L<M, PH, s, XC>(rg, sm, e, pb_out, nLa, covered);
+        store_L<M, PH, s, XC>(rg, sm, e2, pb_out, nLb, covered);
+        if constexpr (s == 0 && GSTOP && XC == 0) {
             xbyte |= (__fadd_rn(Ra, nLa) < 0.f ? 1u : 0u) << e;
             xbyte |= (__fadd_rn(Rb, nLb) < 0.f ? 1u : 0u) << e2;
         }
-        if constexpr (s == 0 && TRACE) {
+        if constexpr (s == 0 && TRACE && XC == 0) {
             a.trace_L[trace_base + ia] = nLa;
             a.trace_L[trace_base + ib] = nLb;
         }
         rg.R[e] = nRa;
         rg.R[e2] = nRb;
     }
-    if constexpr (s == 0 && GSTOP) sm.hd[tid] = (uint8_t)xbyte;
+    if constexpr (s == 0 && GSTOP && XC == 0) sm.hd[tid] = (uint8_t)xbyte;
     if constexpr (snap) {
         uint32_t byte = 0;
 #pragma unroll
@@ -695,12 +710,13 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     if constexpr (TRACE) {
 #pragma unroll
         for (int e = 0; e < EL; ++e)
-            a.trace_R[trace_base + (long long)(s + 1) * N + elem_index<M, PH>(tid, e)] = rg.R[e];
+            a.trace_R[trace_base + (long long)(s + 1) * TSTRIDE + elem_index<M, PH>(tid, e)] = rg.R[e];
     }
-    if constexpr (Q + 1 < G::cnt(PH)) run_stage<M, PH, Q + 1, GSTOP, FREEZE, TRACE>(rg, sm, tid, P0, alpha, a, trace_base);
+    if constexpr (Q + 1 < G::cnt(PH))
+        run_stage<M, PH, Q + 1, GSTOP, FREEZE, TRACE, XC>(rg, sm, tid, P0, alpha, a, trace_base);
 }
 
-template <int M, int PH, bool GSTOP, bool FREEZE, bool TRACE, int CPC>
+template <int M, int PH, bool GSTOP, bool FREEZE, bool TRACE, int CPC, int XC = 0>
 __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, int P0, float alpha,
                                           const CwIO& a, long long trace_base, int grp)
 {
@@ -714,7 +730,7 @@ __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, boo
             for (int e = 0; e < EL; ++e) rg.R[e] = sm.Rx[((PH - 1) & 1) * G::BUF + pb + padded_off<M, PH, SH>(e)];
         }
     }
-    if (worker) run_stage<M, PH, 0, GSTOP, FREEZE, TRACE>(rg, sm, tid, P0, alpha, a, trace_base);
+    if (worker) run_stage<M, PH, 0, GSTOP, FREEZE, TRACE, XC>(rg, sm, tid, P0, alpha, a, trace_base);
     if constexpr (PH + 1 < G::NP) {
         if (worker) {
             constexpr int SH = G::padsh(PH);
@@ -723,7 +739,7 @@ __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, boo
             for (int e = 0; e < EL; ++e) sm.Rx[(PH & 1) * G::BUF + pb + padded_off<M, PH, SH>(e)] = rg.R[e];
         }
         group_sync<G::BLOCK, CPC>(grp);
-        run_phase<M, PH + 1, GSTOP, FREEZE, TRACE, CPC>(rg, sm, tid, worker, P0, alpha, a, trace_base, grp);
+        run_phase<M, PH + 1, GSTOP, FREEZE, TRACE, CPC, XC>(rg, sm, tid, worker, P0, alpha, a, trace_base, grp);
     }
 }
 
@@ -756,22 +772,23 @@ __device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, 
     }
 }
 
-template <int M, int C>
+template <int M, int C, int XC = 0>
 __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int tid, bool worker, const CwIO& a,
                                                 long long trace_base)
 {
     using G = Geo<M>;
+    constexpr long long TSTRIDE = (long long)G::N << XC;
     if constexpr (C <= M) {
         if constexpr (G::is_boundary(C)) {
             constexpr int SH = G::padsh(G::bslot(C));
             for (int i = tid; i < G::N; i += G::BLOCK)
-                a.trace_L[trace_base + (long long)C * G::N + i] = sm.Lb[G::bslot(C) * G::BUF + padded<SH>(i)];
+                a.trace_L[trace_base + C * TSTRIDE + i] = sm.Lb[G::bslot(C) * G::BUF + padded<SH>(i)];
         } else if (worker) {
 #pragma unroll
             for (int e = 0; e < G::EL; ++e)
-                a.trace_L[trace_base + (long long)C * G::N + elem_index<M, G::owner(C)>(tid, e)] = rg.Lr[G::rslot(C)][e];
+                a.trace_L[trace_base + C * TSTRIDE + elem_index<M, G::owner(C)>(tid, e)] = rg.Lr[G::rslot(C)][e];
         }
-        trace_L_columns<M, C + 1>(rg, sm, tid, worker, a, trace_base);
+        trace_L_columns<M, C + 1, XC>(rg, sm, tid, worker, a, trace_base);
     }
 }
 

@@ -38,6 +38,9 @@ cudaError_t launch_m9(const LaunchReq&);
 cudaError_t launch_m10(const LaunchReq&);
 cudaError_t launch_m11(const LaunchReq&);
 cudaError_t launch_m12(const LaunchReq&);
+cudaError_t launch_m13(const LaunchReq&);  // thread-block clusters (bp_cluster.cuh)
+cudaError_t launch_m14(const LaunchReq&);
+cudaError_t launch_m15(const LaunchReq&);
 cudaError_t launch_persistent_m8(const SegLaunch&);
 cudaError_t launch_persistent_m9(const SegLaunch&);
 cudaError_t launch_persistent_m10(const SegLaunch&);
@@ -228,7 +231,7 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     if (batch == 0) return POLARBP_OK;
     if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be device pointers");
     if (trace && (!trace_L || !trace_R || !trace_P)) return fail(POLARBP_ERR_ARG, "trace buffers must be given");
-    if (c->m > 12) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 4096 in this build");
+    if (c->m > 15) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 32768 in this build");
     int rc = check_device(c);
     if (rc != POLARBP_OK) return rc;
 
@@ -262,7 +265,10 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     case 9: e = polarbp::launch_m9(q); break;
     case 10: e = polarbp::launch_m10(q); break;
     case 11: e = polarbp::launch_m11(q); break;
-    default: e = polarbp::launch_m12(q); break;
+    case 12: e = polarbp::launch_m12(q); break;
+    case 13: e = polarbp::launch_m13(q); break;
+    case 14: e = polarbp::launch_m14(q); break;
+    default: e = polarbp::launch_m15(q); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     return POLARBP_OK;

@@ -258,9 +258,13 @@ def test_empty_batch_and_errors(B):
         B.polarbp_decode(code, llr, 5, scale=float("nan"))
     with pytest.raises(B.PolarBPError):
         B.polarbp_decode(code, llr, 5, stop_mode=7)
+    # long codes run on thread-block clusters, but not in the persistent mixed-length launch
     big = B.polarbp_construct(8192, 4096)
+    z = torch.zeros((1, 8192), dtype=torch.float32, device="cuda")
+    seg = (big, z, torch.empty((1, 8192), dtype=torch.uint8, device="cuda"),
+           torch.empty(1, dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int64, device="cuda"))
     with pytest.raises(B.PolarBPError) as e:
-        B.polarbp_decode(big, torch.zeros((1, 8192), dtype=torch.float32, device="cuda"), 5)
+        B.polarbp_decode_segments([seg], 5)
     assert e.value.code == B.POLARBP_ERR_UNSUPPORTED
 
 
