@@ -167,29 +167,45 @@ __device__ __forceinline__ void xform4(uint32_t (&v)[4], int S, int lane)
     }
 }
 
-// Pointer to the same shared-memory object in block `rank` of the cluster.
-template <typename Tp>
-__device__ __forceinline__ Tp* peer_ptr(cg::cluster_group& cl, Tp* local, int rank)
+// Distributed shared memory: the 32-bit cluster address of a local shared-memory
+// object in block `rank` (mapa), and plain loads from such addresses.  The asm is
+// volatile with a memory clobber so that no load moves across a cluster barrier
+// and no mapped address is hoisted into a long-lived register.
+__device__ __forceinline__ uint32_t peer_addr(const void* local, int rank)
 {
-    return cl.map_shared_rank(local, (unsigned)rank);
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(a)
+                 : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ uint32_t ld_peer_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_peer_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
 }
 
-// Warp: xor of the arrays `arr` of the blocks r | x, x ranging over the subsets
-// of the low `bits` rank bits that are clear in r (block r's part of the
-// Eq. (3) transform of a vector spanning those 2^bits blocks).  Four words per lane.
+// Word w of the xor of the arrays `arr` of the blocks r | x, x ranging over the
+// subsets of the low `bits` rank bits that are clear in r: block r's part of the
+// Eq. (3) transform of a vector spanning those 2^bits blocks.  The loop is
+// unrolled over every possible x so that the remote loads are in flight together.
 template <int XC>
-__device__ __forceinline__ void xor_supersets(cg::cluster_group& cl, uint32_t* arr, int r, int bits, uint32_t (&out)[4],
-                                              int lane)
+__device__ __forceinline__ uint32_t xor_supersets(cg::cluster_group& cl, uint32_t* arr, int r, int bits, int w)
 {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = arr[32 * q + lane];
+    uint32_t out = arr[w];
     const int free = ((1 << bits) - 1) & ~r;
-#pragma unroll 1
-    for (int x = free; x; x = (x - 1) & free) {
-        const uint32_t* p = peer_ptr(cl, arr, r | x);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[q] ^= p[32 * q + lane];
+    for (int x = 1; x < (1 << XC); ++x) {
+        if ((x & ~free) == 0) out ^= ld_peer_u32(peer_addr(arr + w, r | x));
     }
+    return out;
 }
 
 // Warp: Eqs. (2)-(4) for every CSFG of local stage jl (1..12) of this block's
@@ -360,8 +376,8 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
             const int pr = r ^ (1 << bitp);
             const bool aside = ((r >> bitp) & 1) == 0;
             const float* Lown = cs.Lcol(s + 1);
-            const float* Lpeer = peer_ptr(cl, cs.Lcol(s + 1), pr);
-            const float* Rpeer = s == 0 ? cs.LlrP : peer_ptr(cl, sm.Rx + (s & 1) * GL::BUF, pr);
+            const uint32_t Lpeer = peer_addr(cs.Lcol(s + 1) + tid, pr);
+            const uint32_t Rpeer = peer_addr(sm.Rx + (s & 1) * GL::BUF + tid, pr);
             // the CSFG of stage s holding this block spans blocks [(r >> (XC-s)) << (XC-s), ...)
             const bool covered = FREEZE && s > 0 && ((((r >> (XC - s)) + 1) << (M - s)) <= P0);
             uint32_t xbits = 0;
@@ -372,8 +388,8 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
 #pragma unroll
             for (int e = 0; e < EL; ++e) {
                 const int i = e * T + tid;
-                Lpv[e] = Lpeer[i];
-                Rpv[e] = Rpeer[i];
+                Lpv[e] = ld_peer_f32(Lpeer + 4 * e * T);
+                Rpv[e] = s == 0 ? cs.LlrP[i] : ld_peer_f32(Rpeer + 4 * e * T);
                 Lov[e] = Lown[i];
             }
 #pragma unroll
@@ -448,32 +464,27 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
             }
             if (GSTOP && warp == 12 + XC) uhat_transform<XC>(sm, Ploc0, cs.Wg, lane);
             cl.sync();  // B1
-            // ---- C2: combine the parts of CSFGs and of the G test that span blocks
-            if (FREEZE && warp >= 12 && warp < 11 + XC) {
-                const int j = warp - 11;  // 1..XC-1
-                uint32_t u[4];
-                xor_supersets<XC>(cl, cs.v(j), r, XC - j, u, lane);
-                bool bad = false;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    cs.uc(j)[32 * q + lane] = u[q];
-                    bad |= (u[q] & sm.Fz[32 * q + lane]) != 0u;
+            // ---- C2: combine the parts of CSFGs and of the G test that span blocks;
+            // four warps per task, one word per lane
+            {
+                constexpr int NX = FREEZE ? XC - 1 : 0;  // stages 1..XC-1
+                const int task = warp >> 2, w = 32 * (warp & 3) + lane;
+                if (task < NX) {
+                    const int j = task + 1;
+                    const uint32_t u = xor_supersets<XC>(cl, cs.v(j), r, XC - j, w);
+                    cs.uc(j)[w] = u;
+                    if (__any_sync(kFull, (u & sm.Fz[w]) != 0u) && lane == 0) atomicOr(&cs.cc[CC_FLAGS], 1 << j);
+                } else if (GSTOP && task == NX) {
+                    const uint32_t x = xor_supersets<XC>(cl, cs.Wg, r, XC, w);
+                    if (__any_sync(kFull, x != cs.xw(0)[w]) && lane == 0)
+                        atomicOr(&cs.cc[CC_FLAGS], (int)0x80000000u);
                 }
-                if (__any_sync(kFull, bad) && lane == 0) atomicOr(&cs.cc[CC_FLAGS], 1 << j);
-            }
-            if (GSTOP && warp == 12 + XC) {
-                uint32_t x[4];
-                xor_supersets<XC>(cl, cs.Wg, r, XC, x, lane);
-                bool diff = false;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) diff |= x[q] != cs.xw(0)[32 * q + lane];
-                if (__any_sync(kFull, diff) && lane == 0) atomicOr(&cs.cc[CC_FLAGS], (int)0x80000000u);
             }
             cl.sync();  // B2
             // ---- C3: the walk over stages 1..M, identical in every block
             if (warp == 0) {
                 int* flc = cs.cc + CC_FLC;
-                if (lane < G::C) flc[lane] = *peer_ptr(cl, cs.cc + CC_FLAGS, lane);
+                if (lane < G::C) flc[lane] = (int)ld_peer_u32(peer_addr(cs.cc + CC_FLAGS, lane));
                 __syncwarp();
                 int P = P0;
                 int Ps = P;
@@ -499,8 +510,8 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
                                 const int owner = P >> (M - XC);
                                 const int jl = j - XC;
                                 const int kl = (P & (n - 1)) >> (12 - jl);
-                                const uint32_t* fb = peer_ptr(cl, cs.Fb, owner);
-                                fail = (fb[fail_word0(jl) + (kl >> 5)] >> (kl & 31)) & 1u;
+                                const uint32_t fw = ld_peer_u32(peer_addr(cs.Fb + fail_word0(jl) + (kl >> 5), owner));
+                                fail = (fw >> (kl & 31)) & 1u;
                             }
                             pass = !fail;
                         }
@@ -640,23 +651,17 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
                     }
                     cl.sync();  // E-barrier 1
                     // E3: enclosing CSFGs spanning blocks; G test on the new prefix
-                    if (warp < XC - 1 && ((evenc >> (warp + 1)) & 1)) {
-                        const int J = warp + 1;
-                        const int lo = cs.cc[CC_EVLO + J], hi = cs.cc[CC_EVHI + J];
-                        if (lo < base + n && hi > base) {
-                            uint32_t v[4];
-                            xor_supersets<XC>(cl, cs.UE, r, XC - J, v, lane);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) cs.xfx(J)[32 * q + lane] = v[q];
+                    {
+                        const int task = warp >> 2, w = 32 * (warp & 3) + lane;
+                        if (task < XC - 1) {
+                            const int J = task + 1;
+                            const int lo = cs.cc[CC_EVLO + J], hi = cs.cc[CC_EVHI + J];
+                            if (((evenc >> J) & 1) && lo < base + n && hi > base)
+                                cs.xfx(J)[w] = xor_supersets<XC>(cl, cs.UE, r, XC - J, w);
+                        } else if (GSTOP && P < N && task == XC - 1) {
+                            const uint32_t x = xor_supersets<XC>(cl, cs.Wg, r, XC, w);
+                            if (__any_sync(kFull, x != cs.xw(0)[w]) && lane == 0) atomicOr(&cs.cc[CC_FLAGS2], 1);
                         }
-                    }
-                    if (GSTOP && P < N && warp == G::NWARP - 1) {
-                        uint32_t x[4];
-                        xor_supersets<XC>(cl, cs.Wg, r, XC, x, lane);
-                        bool diff = false;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) diff |= x[q] != cs.xw(0)[32 * q + lane];
-                        if (__any_sync(kFull, diff) && lane == 0) cs.cc[CC_FLAGS2] = 1;
                     }
                     __syncthreads();
                     // feedback (-1)^x_hat * inf on every frozen CSFG's own L column
@@ -681,10 +686,13 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
                     }
                     cl.sync();  // E-barrier 2: feedback visible to the partners
                     if (GSTOP && P < N) {
-                        int f = 0;
-#pragma unroll 1
-                        for (int q = 0; q < G::C; ++q) f |= *peer_ptr(cl, cs.cc + CC_FLAGS2, q);
-                        done = f == 0;
+                        if (warp == 0) {
+                            const int f = lane < G::C ? (int)ld_peer_u32(peer_addr(cs.cc + CC_FLAGS2, lane)) : 0;
+                            const bool any = __any_sync(kFull, f != 0);
+                            if (lane == 0) cs.cc[CC_DONE] = any ? 0 : 1;
+                        }
+                        __syncthreads();
+                        done = cs.cc[CC_DONE] != 0;
                     }
                 }
             }
