@@ -217,7 +217,7 @@ __device__ __forceinline__ void local_stage_checks(Smem<12>& sm, CSmem<XC>& cs, 
     const int S = 1 << (12 - jl);
     uint32_t u[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) u[q] = hd_word(sm.hd + jl * HDS, snap_lo<12>(jl), 32 * (32 * q + lane));
+    for (int q = 0; q < 4; ++q) u[q] = snap_word<12>(sm.hd, jl, 32 * (32 * q + lane));
     xform4(u, S, lane);
     uint32_t bad[4];
 #pragma unroll
@@ -277,7 +277,7 @@ __device__ __forceinline__ void uhat_transform(Smem<12>& sm, int Ploc, uint32_t*
         if (Ploc >= 32 * (w + 1)) cov = kFull;
         else if (Ploc <= 32 * w) cov = 0u;
         else cov = (1u << (Ploc - 32 * w)) - 1u;
-        const uint32_t hdm = hd_word(sm.hd + 12 * HDS, 0, 32 * w);
+        const uint32_t hdm = snap_word<12>(sm.hd, 12, 32 * w);
         u[q] = (sm.U[w] & cov) | (hdm & ~sm.Fz[w] & ~cov);
     }
     xform4(u, 4096, lane);
@@ -581,11 +581,11 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
                                     for (int q = 0; q < 4; ++q) {
                                         const int w = 32 * q + lane;
                                         x[q] = (w < (S >> 5))
-                                                   ? hd_word(sm.hd + jl * GL::HDS, snap_lo<12>(jl), llo + 32 * w)
+                                                   ? snap_word<12>(sm.hd, jl, llo + 32 * w)
                                                    : 0u;
                                     }
                                 } else {
-                                    x[0] = (hd_word(sm.hd + jl * GL::HDS, snap_lo<12>(jl), llo & ~31) >> (llo & 31)) &
+                                    x[0] = (snap_word<12>(sm.hd, jl, llo & ~31) >> (llo & 31)) &
                                            low_mask(S);
                                     x[1] = x[2] = x[3] = 0u;
                                 }

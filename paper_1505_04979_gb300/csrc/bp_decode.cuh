@@ -175,7 +175,9 @@ struct SmemLayout {
     static constexpr int CTL_INTS = CTL_EV + 2 * (M + 1);
     static constexpr size_t off_Hd = (off_Ctl + sizeof(int) * CTL_INTS + 15) / 16 * 16;
     static constexpr size_t hd_bytes = (size_t)(M + 1) * G::HDS;
-    static constexpr size_t bytes = (off_Hd + hd_bytes + 15) / 16 * 16;
+    // two NW-word buffers for the encoding of the channel-side decisions
+    static constexpr size_t off_Ge = (off_Hd + hd_bytes + 15) / 16 * 16;
+    static constexpr size_t bytes = (off_Ge + 2 * sizeof(uint32_t) * NW + 15) / 16 * 16;
 };
 
 template <int M>
@@ -189,10 +191,12 @@ struct Smem {
     int* ctl;
     uint8_t* hd;    // [(M+1)][HDS] hard-decision snapshots (one byte per thread)
     float* L0;      // column 0 of a sweep that is the lower part of a larger code (else unused)
+    uint32_t* Ge;   // [2][NW] encoding of HD(R[0] + L[0]), built during the sweep
     __device__ __forceinline__ explicit Smem(unsigned char* base)
     {
         L0 = nullptr;
         using L = SmemLayout<M>;
+        Ge = reinterpret_cast<uint32_t*>(base + L::off_Ge);
         Lb = reinterpret_cast<float*>(base + L::off_Lb);
         Rx = reinterpret_cast<float*>(base + L::off_Rx);
         llr = reinterpret_cast<float*>(base + L::off_Llr);
@@ -285,6 +289,24 @@ __device__ __forceinline__ int snap_lo(int c)
 {
     const int ph = c == 0 ? 0 : (c - 1) / 3;
     return (ph == Geo<M>::NP - 1) ? 0 : (M - 3 - 3 * ph);
+}
+
+// Codes of N >= 256 (every phase has whole warps) store every snapshot row as
+// natural-order words, written by snap_row below; smaller codes keep one byte
+// per thread and gather with hd_word.
+template <int M>
+__host__ __device__ constexpr bool natural_rows()
+{
+    return M >= 8;
+}
+
+// Decisions of positions [i0, i0 + 32) of snapshot column c.
+template <int M>
+__device__ __forceinline__ uint32_t snap_word(const uint8_t* hd, int c, int i0)
+{
+    const uint8_t* row = hd + c * Geo<M>::HDS;
+    if constexpr (natural_rows<M>()) return reinterpret_cast<const uint32_t*>(row)[i0 >> 5];
+    else return hd_word(row, snap_lo<M>(c), i0);
 }
 
 template <int RW>
@@ -405,7 +427,7 @@ struct Spec {
     int fail;             // bit j: the speculative check of stage j fails Eq. (4)
 };
 
-template <int M>
+template <int M, bool SMALL = true>
 __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int jmin, int lane)
 {
     using SP = Spec<M>;
@@ -426,7 +448,7 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
                 const int base = (P0 >> (M - j)) << (M - j);
                 sp.lvl[r] = j;
                 sp.w[r] = wi;
-                sp.x[r] = hd_word(sm.hd + j * HDS, snap_lo<M>(j), base + 32 * wi);
+                sp.x[r] = snap_word<M>(sm.hd, j, base + 32 * wi);
             }
             uint32_t v = sp.x[r];
 #pragma unroll
@@ -463,7 +485,7 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
             bad_levels |= __reduce_or_sync(kFull, flag);
         }
     }
-    {
+    if constexpr (SMALL) {
         unsigned flag = 0;
         sp.xs = sp.us = 0u;
         if (lane < SP::NS && SP::JS0 + lane >= jmin) {
@@ -471,7 +493,7 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
             const int S = N >> j;
             const int base = (P0 >> (M - j)) << (M - j);
             const uint32_t mk = low_mask(S);
-            const uint32_t xv = (hd_word(sm.hd + j * HDS, snap_lo<M>(j), base & ~31) >> (base & 31)) & mk;
+            const uint32_t xv = (snap_word<M>(sm.hd, j, base & ~31) >> (base & 31)) & mk;
             uint32_t v = xv;
 #pragma unroll
             for (int h = 1; h < 16; h <<= 1) v ^= (v >> h) & xmask(h);  // steps >= S act on zero bits
@@ -535,6 +557,77 @@ __device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
     return (int)__reduce_add_sync(kFull, (unsigned)pe) + (N >> 1);
 }
 
+// G-matrix stop for N >= 256.  F^{(x)M} is its own inverse over GF(2), so
+// u_hat . F^{(x)M} == HD(R[0] + L[0]) holds exactly when u_hat equals the
+// encoding of HD(R[0] + L[0]).  That encoding does not depend on the freezes
+// of the iteration, so the sweep builds it (genc_step) from stage 0 on, spread
+// over every warp, and the test after the freezes is a word-by-word comparison.
+template <int M>
+__host__ __device__ constexpr int genc_steps()
+{
+    return (M - 8 + 1) / 2;  // radix-4 steps over the word-index bits above the warp's 8 words
+}
+
+template <int M, int PH>
+__device__ __forceinline__ void genc_step(Smem<M>& sm, int tid)
+{
+    static_assert(genc_steps<M>() <= Geo<M>::NP - 2, "one radix-4 step per phase boundary after the first");
+    constexpr int NW = Geo<M>::NW;
+    constexpr int LNW = M - 5;  // log2 NW
+    if constexpr (PH == 1) {
+        // each warp: 8 words, in-word butterflies, then across the 8 lanes
+        const int lane = tid & 31, w = 8 * (tid >> 5) + (lane & 7);
+        uint32_t v = snap_word<M>(sm.hd, 0, 32 * w);
+#pragma unroll
+        for (int h = 1; h < 32; h <<= 1) v ^= (v >> h) & xmask(h);
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const uint32_t y = __shfl_xor_sync(kFull, v, d);
+            if (!(lane & d)) v ^= y;
+        }
+        if (lane < 8) sm.Ge[w] = v;
+    } else if constexpr (PH >= 2 && PH - 2 < genc_steps<M>()) {
+        // word-index bits b and b + 1 (b = 3 + 2 (PH - 2)), ping-pong between the two buffers
+        constexpr int b = 3 + 2 * (PH - 2);
+        constexpr bool two = b + 1 < LNW;
+        const uint32_t* src = sm.Ge + ((PH - 2) & 1) * NW;
+        uint32_t* dst = sm.Ge + ((PH - 1) & 1) * NW;
+        if (tid < NW) {
+            const int w = tid;
+            uint32_t v = src[w];
+            const bool c1 = !(w & (1 << b));
+            if (c1) v ^= src[w | (1 << b)];
+            if constexpr (two) {
+                const bool c2 = !(w & (1 << (b + 1)));
+                if (c2) v ^= src[w | (2 << b)];
+                if (c1 && c2) v ^= src[w | (3 << b)];
+            }
+            dst[w] = v;
+        }
+    }
+}
+
+template <int M>
+__device__ __forceinline__ bool gmatrix_ok_pre(Smem<M>& sm, int P, int lane)
+{
+    constexpr int NW = Geo<M>::NW, RW = Geo<M>::RW;
+    const uint32_t* enc = sm.Ge + (genc_steps<M>() & 1) * NW;
+    bool same = true;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int w = 32 * r + lane;
+        if (w < NW) {
+            uint32_t cov;
+            if (P >= 32 * (w + 1)) cov = kFull;
+            else if (P <= 32 * w) cov = 0u;
+            else cov = (1u << (P - 32 * w)) - 1u;
+            const uint32_t u = (sm.U[w] & cov) | (snap_word<M>(sm.hd, M, 32 * w) & ~sm.Fz[w] & ~cov);
+            same &= u == enc[w];
+        }
+    }
+    return __all_sync(kFull, same);
+}
+
 // G-matrix stop: u_hat . F^{(x)M} == HD(R[0] + L[0]).
 template <int M>
 __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
@@ -545,8 +638,8 @@ __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
     for (int r = 0; r < RW; ++r) {
         const int w = 32 * r + lane;
         const bool in = (N >= 32) ? (w < NW) : (lane == 0);
-        u[r] = in ? hd_word(sm.hd + M * HDS, 0, 32 * w) & low_mask(N) : 0u;
-        x[r] = in ? hd_word(sm.hd, snap_lo<M>(0), 32 * w) & low_mask(N) : 0u;
+        u[r] = in ? snap_word<M>(sm.hd, M, 32 * w) & low_mask(N) : 0u;
+        x[r] = in ? snap_word<M>(sm.hd, 0, 32 * w) & low_mask(N) : 0u;
         if (N < 32) {
             u[r] = __shfl_sync(kFull, u[r], 0);
             x[r] = __shfl_sync(kFull, x[r], 0);
@@ -591,7 +684,11 @@ __device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
     }
     bool done = FREEZE && (P >= N);
     if constexpr (GSTOP) {
-        if (!done) done = gmatrix_ok<M>(sm, P, lane);
+        if constexpr (natural_rows<M>()) {
+            if (!done) done = gmatrix_ok_pre<M>(sm, P, lane);
+        } else {
+            if (!done) done = gmatrix_ok<M>(sm, P, lane);
+        }
     }
     __syncwarp();
     if (lane == 0) {
@@ -654,6 +751,74 @@ __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb,
 // of M + XC stages (stage s here is stage s + XC there): P0 is then the covered
 // prefix within this part, stage 0 may be covered, its L column is stored, the
 // channel-side decisions are taken elsewhere and trace columns are N << XC apart.
+// One snapshot row of phase PH from each thread's 8 decisions (bit e of `byte`
+// = element e), in natural order for N >= 256.  Phase PH maps element e of
+// thread t to position (t & (2^lo - 1)) | e << lo | (t >> lo) << (lo + 3):
+//   lo >= 5: the lanes of a warp cover 32 consecutive positions of each
+//            element, so one ballot per element is a word;
+//   lo = 4, 3: a word takes 16 (8) lanes of two (four) elements' ballots,
+//            assembled with byte permutes by lanes 0..7 (one word each);
+//   lo = 2, 1: a word is four consecutive threads' decisions, spread to their
+//            bit positions and or-ed across the four lanes;
+//   lo = 0: each thread's byte is 8 consecutive positions.
+template <int M, int PH>
+__device__ __forceinline__ void snap_row(uint8_t* row, uint32_t byte, int tid)
+{
+    constexpr int lo = Geo<M>::lo(PH);
+    if constexpr (lo == 0 || !natural_rows<M>()) {
+        row[tid] = (uint8_t)byte;
+    } else {
+        uint32_t* w = reinterpret_cast<uint32_t*>(row);
+        const int lane = tid & 31, k = tid >> 5;
+        if constexpr (lo >= 3) {
+            uint32_t b[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) b[e] = __ballot_sync(kFull, (byte >> e) & 1u);
+            if constexpr (lo >= 5) {
+                if (lane == 0) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) w[elem_index<M, PH>(tid & ~31, e) >> 5] = b[e];
+                }
+            } else if constexpr (lo == 4) {
+                // word (e >> 1) | (2k + h) << 2 holds lanes 16h.. of elements 2(e>>1) and 2(e>>1)+1
+                if (lane < 8) {
+                    const int eh = lane & 3, h = lane >> 2;
+                    const uint32_t b0 = eh == 0 ? b[0] : eh == 1 ? b[2] : eh == 2 ? b[4] : b[6];
+                    const uint32_t b1 = eh == 0 ? b[1] : eh == 1 ? b[3] : eh == 2 ? b[5] : b[7];
+                    w[eh | ((2 * k + h) << 2)] = __byte_perm(b0, b1, h ? 0x7632u : 0x5410u);
+                }
+            } else {
+                // lo = 3: word (e >> 2) | (4k + g) << 1 holds byte g of elements 4(e>>2) .. +3
+                if (lane < 8) {
+                    const int eh = lane >> 2, g = lane & 3;
+                    const uint32_t b0 = eh ? b[4] : b[0], b1 = eh ? b[5] : b[1];
+                    const uint32_t b2 = eh ? b[6] : b[2], b3 = eh ? b[7] : b[3];
+                    const uint32_t sel = (uint32_t)g | ((uint32_t)(4 + g) << 4);
+                    w[eh | ((4 * k + g) << 1)] = __byte_perm(__byte_perm(b0, b1, sel), __byte_perm(b2, b3, sel), 0x5410u);
+                }
+            }
+        } else {
+            uint32_t x = byte;
+            if constexpr (lo == 2) {
+                // bit e -> 4e + (t & 3)
+                x = (x | (x << 12)) & 0x000F000Fu;
+                x = (x | (x << 6)) & 0x03030303u;
+                x = (x | (x << 3)) & 0x11111111u;
+                x <<= (tid & 3);
+            } else {
+                // lo = 1: bit e -> 2e + (t & 1) + 16 ((t >> 1) & 1)
+                x = (x | (x << 4)) & 0x0F0Fu;
+                x = (x | (x << 2)) & 0x3333u;
+                x = (x | (x << 1)) & 0x5555u;
+                x <<= (tid & 1) + 16 * ((tid >> 1) & 1);
+            }
+            x |= __shfl_xor_sync(kFull, x, 1);
+            x |= __shfl_xor_sync(kFull, x, 2);
+            if ((tid & 3) == 0) w[tid >> 2] = x;
+        }
+    }
+}
+
 template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE, int XC = 0>
 __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha, const CwIO& a,
                                           long long trace_base)
@@ -700,12 +865,12 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         rg.R[e] = nRa;
         rg.R[e2] = nRb;
     }
-    if constexpr (s == 0 && GSTOP && XC == 0) sm.hd[tid] = (uint8_t)xbyte;
+    if constexpr (s == 0 && GSTOP && XC == 0) snap_row<M, PH>(sm.hd, xbyte, tid);
     if constexpr (snap) {
         uint32_t byte = 0;
 #pragma unroll
         for (int e = 0; e < EL; ++e) byte |= (rg.R[e] < 0.f ? 1u : 0u) << e;
-        sm.hd[(s + 1) * G::HDS + tid] = (uint8_t)byte;
+        snap_row<M, PH>(sm.hd + (s + 1) * G::HDS, byte, tid);
     }
     if constexpr (TRACE) {
 #pragma unroll
@@ -729,6 +894,7 @@ __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, boo
 #pragma unroll
             for (int e = 0; e < EL; ++e) rg.R[e] = sm.Rx[((PH - 1) & 1) * G::BUF + pb + padded_off<M, PH, SH>(e)];
         }
+        if constexpr (GSTOP && XC == 0 && natural_rows<M>()) genc_step<M, PH>(sm, tid);
     }
     if (worker) run_stage<M, PH, 0, GSTOP, FREEZE, TRACE, XC>(rg, sm, tid, P0, alpha, a, trace_base);
     if constexpr (PH + 1 < G::NP) {
