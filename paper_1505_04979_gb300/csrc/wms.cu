@@ -17,8 +17,9 @@
 // One block of N/2 threads (at least 32) per codeword, one PE per thread per
 // stage, all message planes in shared memory; the forward checkpoints L and R
 // after every iteration to the caller's workspace, the adjoint reads them back
-// in reverse order and writes one gradient partial per codeword, which a
-// second kernel sums over the batch in a fixed order.
+// in reverse order and writes one gradient partial per codeword, which two
+// more kernels sum over the batch in a fixed order (chunks of codewords, then
+// the chunks).
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -128,8 +129,7 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
     const int p = threadIdx.x;
     const size_t W = (size_t)T * m * (N / 2);
     for (int t = T - 1; t >= 0; --t) {
-        const float* Lc = ckpt + ((size_t)cw * T + t) * 2 * plane;                            // L^t
-        const float* Rc = Lc + plane;                                                         // R^t
+        const float* Rc = ckpt + ((size_t)cw * T + t) * 2 * plane + plane;                   // R^t
         const float* Lp = t > 0 ? ckpt + ((size_t)cw * T + (t - 1)) * 2 * plane : L0;         // L^{t-1}
         for (int k = threadIdx.x; k < plane; k += blockDim.x) {
             dR[k] = 0.f;
@@ -150,8 +150,10 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
                 const float Ra = Rc[s * N + a], Rb = Rc[s * N + b];
                 const float tt = __fadd_rn(Lb, Rb);
                 const float g = wmin(wt, La, Ra);
-                const float oLa = Lc[s * N + a], oLb = Lc[s * N + b];
-                const float oRa = Rc[(s + 1) * N + a], oRb = Rc[(s + 1) * N + b];
+                // the stage's forward outputs, recomputed from its inputs exactly as the
+                // forward formed them (only their infinities matter here)
+                const float oLa = wmin(wt, La, tt), oLb = __fadd_rn(Lb, g);
+                const float oRa = wmin(wt, Ra, tt), oRb = __fadd_rn(Rb, g);
                 const float gLa = (s >= 1 && !isinf(oLa)) ? dL[s * N + a] : 0.f;
                 const float gLb = (s >= 1 && !isinf(oLb)) ? dL[s * N + b] : 0.f;
                 const float gRa = isinf(oRa) ? 0.f : dR[(s + 1) * N + a];
@@ -204,13 +206,31 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
     }
 }
 
-// dw[k] = sum over codewords of partial[cw][k], in codeword order
-__global__ void wms_reduce_kernel(const float* __restrict__ partial, int batch, size_t W, float* __restrict__ dw)
+// Deterministic batch sum of the per-codeword gradient partials, in two fixed
+// passes: chunk[q][k] = sum of partial[c][k] over the kReduceChunk codewords of
+// chunk q in codeword order (grid: weight tiles x chunks), then dw[k] = sum of
+// chunk[q][k] in chunk order.
+constexpr int kReduceChunk = 64;
+
+__global__ void wms_reduce_chunks_kernel(const float* __restrict__ partial, int batch, size_t W,
+                                         float* __restrict__ chunk)
+{
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (k >= W) return;
+    const int c0 = q * kReduceChunk, c1 = min(batch, c0 + kReduceChunk);
+    float acc_v = 0.f;
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) acc_v += partial[(size_t)c * W + k];
+    chunk[(size_t)q * W + k] = acc_v;
+}
+
+__global__ void wms_reduce_kernel(const float* __restrict__ chunk, int nchunks, size_t W, float* __restrict__ dw)
 {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= W) return;
     float acc_v = 0.f;
-    for (int c = 0; c < batch; ++c) acc_v += partial[(size_t)c * W + k];
+    for (int q = 0; q < nchunks; ++q) acc_v += chunk[(size_t)q * W + k];
     dw[k] = acc_v;
 }
 
@@ -232,14 +252,17 @@ int check_device(const polarbp_code* c);
 
 namespace {
 struct WmsLayout {
-    size_t ckpt, partial, total;
+    size_t ckpt, partial, chunk, total;
 };
 WmsLayout wms_layout(int N, int m, int batch, int T)
 {
     WmsLayout l;
+    const size_t W = (size_t)T * m * (N / 2);
+    const size_t nchunks = ((size_t)batch + kReduceChunk - 1) / kReduceChunk;
     l.ckpt = 0;
     l.partial = align256((size_t)batch * T * 2 * (m + 1) * N * sizeof(float));
-    l.total = align256(l.partial + (size_t)batch * T * m * (N / 2) * sizeof(float));
+    l.chunk = align256(l.partial + (size_t)batch * W * sizeof(float));
+    l.total = align256(l.chunk + nchunks * W * sizeof(float));
     return l;
 }
 
@@ -324,7 +347,13 @@ int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, 
                                                      partial, dllr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "wms backward launch");
-    wms_reduce_kernel<<<(unsigned)((W + 255) / 256), 256, 0, s>>>(partial, batch, W, dweights);
+    float* chunk = reinterpret_cast<float*>(static_cast<char*>(workspace) + l.chunk);
+    const int nchunks = (batch + kReduceChunk - 1) / kReduceChunk;
+    wms_reduce_chunks_kernel<<<dim3((unsigned)((W + 255) / 256), (unsigned)nchunks), 256, 0, s>>>(partial, batch, W,
+                                                                                                  chunk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wms reduce launch");
+    wms_reduce_kernel<<<(unsigned)((W + 255) / 256), 256, 0, s>>>(chunk, nchunks, W, dweights);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "wms reduce launch");
     return POLARBP_OK;
