@@ -198,6 +198,21 @@ def cpu_baseline(target_s: float = 12.0):
             "avg_iters": float(it.mean())}
 
 
+def oracle_code_sample(N: int, K: int, idx, ebn0, max_iter: int, seed: int):
+    """Time the FP64 oracle (threaded over codewords) on the host-generated codewords `idx` of an
+    (N, K) code, G-matrix stop + CSFG freezing; ebn0 is a scalar or one value per codeword."""
+    from oracle import oracle as O
+    from paper_1505_04979_gb300 import inputs as I
+    fz = O.bec_frozen(N, K)
+    idx = np.asarray(idx)
+    u = I.info_bits(seed, idx, fz)
+    x = O.encode(u)
+    llr = I.channel_llr(x, I.gaussian(seed, idx, N), I.sigma(ebn0, K / N))
+    t0 = time.perf_counter()
+    O.decode_batch(fz, llr, max_iter, ALPHA, 1, 1)
+    return time.perf_counter() - t0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -452,6 +467,23 @@ def run_mixed(args):
                          "peak": PEAK_PE_PER_S / 1e9, "unit": "GPE/s",
                          "frac": pe_total / (ms_graph * 1e-3) / PEAK_PE_PER_S},
             "classes": per, "clocks": clk.summary(), "gpu_launches": args.steps * len({c[0] for c in MIXED_CLASSES})}
+    if not args.skip_cpu:
+        # the oracle on a sample of the same stream: the first codewords of each class
+        from oracle import oracle as O
+        from paper_1505_04979_gb300 import inputs as I
+        O.build()
+        bits, secs, ncw = 0.0, 0.0, 0
+        for k, (n_, k_) in enumerate(MIXED_CLASSES):
+            members = idx[cls == k][: max(8, 16384 // n_)]
+            eb = I.uniform(seed, members, 1.5, 3.5)
+            dt = oracle_code_sample(n_, k_, members, eb, MAX_ITER, seed)
+            bits += k_ * len(members)
+            secs += dt
+            ncw += len(members)
+        line["cpu_baseline"] = {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": O.max_threads(),
+                                "kind": "oracle",
+                                "sample": (f"{ncw} codewords of the stream (the first of each class), FP64 oracle "
+                                           f"threaded over codewords, {secs:.1f} s")}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -469,10 +501,10 @@ def run_long(args):
     stream = torch.cuda.current_stream()
     points, tot_bits, tot_ms, tot_pe = {}, 0.0, 0.0, 0.0
     with ClockSampler(0) as clk:
-        for N in (8192, 16384, 32768):
+        for N in ((args.long_n,) if args.long_n else (8192, 16384, 32768)):
             K = N // 2
             code = B.polarbp_construct(N, K)
-            for eb in (2.0, 2.5, 3.0):
+            for eb in ((args.long_ebn0,) if args.long_ebn0 is not None else (2.0, 2.5, 3.0)):
                 u, llr = B.polarbp_awgn(code, SEED + 3, 0, n_cw, eb)
                 uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
                 it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
@@ -499,16 +531,29 @@ def run_long(args):
                 tot_pe += pe_sum
                 del u, llr, uh, it, pe
                 torch.cuda.empty_cache()
+    cpu = None
+    if not args.skip_cpu:
+        from oracle import oracle as O
+        O.build()
+        bits, secs, parts = 0.0, 0.0, []
+        for N, cnt in ((8192, 64), (16384, 32), (32768, 16)):
+            dt = oracle_code_sample(N, N // 2, np.arange(cnt), 2.5, 100, SEED + 3)
+            bits += cnt * (N // 2)
+            secs += dt
+            parts.append(f"{cnt} x N={N}")
+        cpu = {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": O.max_threads(), "kind": "oracle",
+               "sample": (", ".join(parts) + " codewords at 2.5 dB, G-matrix stop + CSFG freezing, max 100 "
+                          f"iterations, FP64 oracle threaded over codewords, {secs:.1f} s")}
     line = {"metric": "info Gbit/s/GB300, long codes N in {8192,16384,32768}, Eb/N0 {2.0,2.5,3.0} dB",
             "value": tot_bits / (tot_ms * 1e-3) / 1e9, "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"long codes, K=N/2, {n_cw} codewords per point, 9 points per step, "
+            "config": {"workload": f"long codes, K=N/2, {n_cw} codewords per point, {len(points)} points per step, "
                                    "G-matrix stop + CSFG freezing, max 100 iterations, thread-block clusters",
                        "l2": "inputs larger than L2 (13 GB of LLRs at N=32768)"},
             "roofline": {"bound": "alu", "achieved": tot_pe / (tot_ms * 1e-3) / 1e9, "peak": PEAK_PE_PER_S / 1e9,
                          "unit": "GPE/s", "frac": tot_pe / (tot_ms * 1e-3) / PEAK_PE_PER_S},
-            "points": points, "clocks": clk.summary(), "gpu_launches": 9 * args.steps}
+            "points": points, "clocks": clk.summary(), "gpu_launches": len(points) * args.steps, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -606,6 +651,28 @@ def run_wms(args):
                          "achieved": results["N=256"]["backward_GBps"],
                          "frac": results["N=256"]["backward_hbm_frac"], "kernel": "wms_backward_kernel"},
             "results": results}
+    if not args.skip_cpu:
+        # the oracle's forward and adjoint (FP64, one thread) on a sample of N = 256 training codewords
+        from oracle import oracle as O
+        O.build()
+        N, K = 256, 128
+        m = 8
+        fz = O.bec_frozen(N, K)
+        idx = np.arange(256)
+        u = I.info_bits(SEED + 5, idx, fz)
+        x = O.encode(u)
+        eb = I.uniform(SEED + 5, idx, 1.0, 4.0)
+        llr = I.channel_llr(x, I.gaussian(SEED + 5, idx, N), I.sigma(eb, K / N))
+        wts = np.full((T, m, N // 2), ALPHA)
+        dout = np.ones(N)
+        t0 = time.perf_counter()
+        for c in range(len(idx)):
+            O.wms_forward(fz, llr[c], wts)
+            O.wms_backward(fz, llr[c], wts, dout)
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(idx) / secs, "unit": "codewords/s", "cores": 1, "kind": "oracle",
+                                "sample": (f"{len(idx)} training codewords at N=256, T={T}: FP64 oracle forward and "
+                                           f"adjoint, one thread, {secs:.1f} s")}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -626,6 +693,8 @@ def main():
                     help="n1024: the (1024,512) headline; mixed: the mixed-length stream; long: N = 8192..32768 "
                          "on thread-block clusters; wms: learned weights")
     ap.add_argument("--long-codewords", type=int, default=100000)
+    ap.add_argument("--long-n", type=int, default=0, help="one code length of the long workload (default: all)")
+    ap.add_argument("--long-ebn0", type=float, default=None, help="one Eb/N0 point of the long workload")
     ap.add_argument("--wms-steps", type=int, default=300)
     ap.add_argument("--wms-lr", type=float, default=0.005)
     ap.add_argument("--wms-eval", type=int, default=1 << 17)
