@@ -585,7 +585,7 @@ def run_wms(args):
         opt = torch.optim.Adam([w], lr=args.wms_lr)
         ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
         losses, fwd_ms, bwd_ms = [], 0.0, 0.0
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1, e1b, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         for step in range(args.wms_steps):
             ebn0 = torch.from_numpy(I.uniform(SEED + 5, np.arange(step * batch, (step + 1) * batch), 1.0, 4.0)
                                     .astype(np.float32)).cuda()
@@ -600,6 +600,7 @@ def run_wms(args):
             loss.backward()
             dout = torch.zeros((batch, N), dtype=torch.float32, device="cuda")
             dout[:, info] = -x.grad
+            e1b.record(stream)
             dw, _ = B.polarbp_wms_backward(code, llr, w.detach(), dout, ws)
             e2.record(stream)
             w.grad = dw
@@ -607,7 +608,7 @@ def run_wms(args):
             torch.cuda.synchronize()
             if step >= 3:
                 fwd_ms += e0.elapsed_time(e1)
-                bwd_ms += e1.elapsed_time(e2)
+                bwd_ms += e1b.elapsed_time(e2)
             losses.append(float(loss.detach()))
         timed = max(1, args.wms_steps - 3)
         fwd_ms /= timed

@@ -117,12 +117,9 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
     float* dL = sh;            // adjoint of the L state after the current iteration
     float* dLp = sh + plane;   // adjoint of the L state before it
     float* dR = sh + 2 * plane;
-    float* L0 = sh + 3 * plane;  // the L state before iteration 1
     const long long cw = blockIdx.x;
     for (int k = threadIdx.x; k < plane; k += blockDim.x) {
-        const int c = k / N, i = k % N;
         dL[k] = 0.f;
-        L0[k] = (c == m) ? (((frozen_words[i >> 5] >> (i & 31)) & 1u) ? INFINITY : 0.f) : 0.f;
     }
     float dl_acc[4] = {0.f, 0.f, 0.f, 0.f};  // dllr of positions threadIdx.x + j blockDim.x (N <= 4 blockDim.x)
     __syncthreads();
@@ -130,7 +127,8 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
     const size_t W = (size_t)T * m * (N / 2);
     for (int t = T - 1; t >= 0; --t) {
         const float* Rc = ckpt + ((size_t)cw * T + t) * 2 * plane + plane;                   // R^t
-        const float* Lp = t > 0 ? ckpt + ((size_t)cw * T + (t - 1)) * 2 * plane : L0;         // L^{t-1}
+        // L^{t-1}; before iteration 1 it is the prior (+inf on frozen positions of column m, else 0)
+        const float* Lp = t > 0 ? ckpt + ((size_t)cw * T + (t - 1)) * 2 * plane : nullptr;
         for (int k = threadIdx.x; k < plane; k += blockDim.x) {
             dR[k] = 0.f;
             dLp[k] = 0.f;
@@ -146,7 +144,14 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
                 const int a = pair_a(m, s, p), b = a + h;
                 const size_t widx = ((size_t)t * m + s) * (N / 2) + p;
                 const float wt = __ldg(w + widx);
-                const float La = Lp[(s + 1) * N + a], Lb = Lp[(s + 1) * N + b];
+                float La = 0.f, Lb = 0.f;
+                if (Lp) {
+                    La = Lp[(s + 1) * N + a];
+                    Lb = Lp[(s + 1) * N + b];
+                } else if (s + 1 == m) {
+                    La = ((frozen_words[a >> 5] >> (a & 31)) & 1u) ? INFINITY : 0.f;
+                    Lb = ((frozen_words[b >> 5] >> (b & 31)) & 1u) ? INFINITY : 0.f;
+                }
                 const float Ra = Rc[s * N + a], Rb = Rc[s * N + b];
                 const float tt = __fadd_rn(Lb, Rb);
                 const float g = wmin(wt, La, Ra);
@@ -336,7 +341,7 @@ int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, 
     rc = check_device(code);
     if (rc != POLARBP_OK) return rc;
     const int threads = N / 2 < 32 ? 32 : N / 2;
-    const size_t smem = 4 * (size_t)(m + 1) * N * sizeof(float);
+    const size_t smem = 3 * (size_t)(m + 1) * N * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(wms_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "wms backward attribute");
