@@ -316,3 +316,28 @@ def test_full_size_launch_sampled(B):
         assert np.array_equal(pe[sel].cpu().numpy(), ope)
         if mode == (0, 0):
             assert int(it.min()) == 60 and int(it.max()) == 60
+
+
+def test_n8_freeze_hand_trace(B):
+    """The (8,4) freezing example worked by hand (tests/golden/n8_freeze_hand_trace.json): every
+    value is a small integer, exact in binary32, so the kernel must reproduce it exactly."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "n8_freeze_hand_trace.json")))
+    code = B.polarbp_construct(8, 4)
+    assert np.array_equal(code.frozen_mask(), np.array(g["frozen"], np.uint8))
+    d = torch.tensor([g["llr"]], dtype=torch.float32, device="cuda")
+    for stop in (0, 1):
+        uh, it, pe, tL, tR, tP = B.polarbp_decode_trace(code, d, g["max_iter"], g["alpha"], stop, 1)
+        torch.cuda.synchronize()
+        assert int(it[0]) == g["max_iter"]
+        assert int(pe[0]) == sum(x["pe"] for x in g["iterations"])
+        assert np.array_equal(uh.cpu().numpy()[0], np.array(g["u_hat"], np.uint8))
+        tL, tR, tP = tL.cpu().numpy(), tR.cpu().numpy(), tP.cpu().numpy()
+        for t, x in enumerate(g["iterations"]):
+            assert tP[0, t] == x["P"]
+            for plane, arr in (("R", tR), ("L", tL)):
+                for c, vals in x[plane].items():
+                    for i, v in vals.items():
+                        want = np.inf if v == "inf" else float(v)
+                        assert arr[0, t, int(c), int(i)] == want, (stop, t, plane, c, i)

@@ -337,3 +337,25 @@ def test_statistics_at_3db_are_plausible():
     assert 18.0 < res[(1, 0)][1] < 32.0
     assert res[(1, 1)][2] <= res[(1, 0)][2]
     assert res[(0, 1)][2] < res[(0, 0)][2]
+
+
+def test_n8_freeze_hand_trace():
+    """Two iterations of the (8,4) code with freezing, worked by hand (Eq. (1), Eqs. (2)-(4),
+    Sec. III freezing order, Sec. IV count): a stage-1 CSFG freezes after stage 0 of iteration 1,
+    the later stages skip its PEs, every later check fails, and the G test does not stop."""
+    g = json.load(open(os.path.join(GOLDEN, "n8_freeze_hand_trace.json")))
+    fz = np.array(g["frozen"], np.uint8)
+    llr = np.array(g["llr"], np.float32)
+    for stop in (0, 1):
+        o = O.decode(fz, llr, g["max_iter"], g["alpha"], stop, 1, trace=True)
+        assert o["iters"] == g["max_iter"]
+        assert o["pe"] == sum(it["pe"] for it in g["iterations"])
+        assert np.array_equal(o["u_hat"], np.array(g["u_hat"], np.uint8))
+        for t, it in enumerate(g["iterations"]):
+            assert o["P"][t] == it["P"]
+            assert o["pe_iter"][t] == it["pe"]
+            for plane, key in (("R", "R"), ("L", "L")):
+                for c, vals in it[key].items():
+                    for i, v in vals.items():
+                        want = np.inf if v == "inf" else float(v)
+                        assert o[plane][t][int(c), int(i)] == want, (stop, t, plane, c, i)
