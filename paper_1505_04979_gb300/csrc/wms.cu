@@ -61,7 +61,7 @@ __global__ void wms_forward_kernel(const float* __restrict__ llr, const uint32_t
                                    const float* __restrict__ w, int N, int m, int T, float* __restrict__ out,
                                    float* __restrict__ ckpt)
 {
-    extern __shared__ float sh[];
+    extern __shared__ __align__(16) float sh[];
     float* L = sh;                        // (m+1) N
     float* R = sh + (size_t)(m + 1) * N;  // (m+1) N
     const long long cw = blockIdx.x;
@@ -92,10 +92,13 @@ __global__ void wms_forward_kernel(const float* __restrict__ llr, const uint32_t
             }
             __syncthreads();
         }
-        float* dst = ckpt + ((size_t)cw * T + t) * 2 * plane;
-        for (int k = threadIdx.x; k < plane; k += blockDim.x) {
-            dst[k] = L[k];
-            dst[plane + k] = R[k];
+        // checkpoint: both planes with 16-byte stores ((m+1) N is a multiple of 4)
+        float4* dst = reinterpret_cast<float4*>(ckpt + ((size_t)cw * T + t) * 2 * plane);
+        const float4* L4 = reinterpret_cast<const float4*>(L);
+        const float4* R4 = reinterpret_cast<const float4*>(R);
+        for (int k = threadIdx.x; k < plane / 4; k += blockDim.x) {
+            dst[k] = L4[k];
+            dst[plane / 4 + k] = R4[k];
         }
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) out[cw * N + i] = __fadd_rn(R[m * N + i], L[m * N + i]);
