@@ -192,10 +192,17 @@ def cpu_baseline(target_s: float = 12.0):
     count = int(min(60000, max(512, rate * target_s)))
     dt, uh, u, it, pe = oracle_time(count, first=1 << 40)
     value = count * K / dt / 1e9
+    # the single-core figure on a tenth of the sample
+    fz, _, llr1 = oracle_inputs(max(64, count // 10), 1 << 40)
+    t0 = time.perf_counter()
+    O.decode_batch(fz, llr1, MAX_ITER, ALPHA, 1, 1, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": value, "unit": "Gbit/s", "cores": O.max_threads(), "kind": "oracle",
             "sample": (f"{count} codewords of the same workload ((1024,512), 3.0 dB, G-matrix stop + CSFG "
                        f"freezing, max 60 iterations), FP64 oracle threaded over codewords, {dt:.1f} s"),
-            "avg_iters": float(it.mean())}
+            "avg_iters": float(it.mean()),
+            "single_core": {"value": llr1.shape[0] * K / dt1 / 1e9, "unit": "Gbit/s",
+                            "codewords_per_s": llr1.shape[0] / dt1, "sample": f"{llr1.shape[0]} codewords, 1 thread"}}
 
 
 def oracle_code_sample(N: int, K: int, idx, ebn0, max_iter: int, seed: int):
@@ -488,6 +495,56 @@ def run_mixed(args):
     return 0
 
 
+def run_sweep(args):
+    """FER sweep of the (1024,512) code: Eb/N0 1.0 .. 3.5 dB in 0.5 dB steps, the three modes
+    (fixed iterations, G-matrix stop, G-matrix stop + CSFG freezing) at max 60 iterations on the
+    same codewords, 10^6 codewords per point (device generator), and the three modes at max 40
+    iterations at 3.0 dB (the paper's setting)."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    n_cw = args.sweep_codewords
+    code = B.polarbp_construct(N, K)
+    stream = torch.cuda.current_stream()
+    uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
+    it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
+    pe = torch.empty(n_cw, dtype=torch.int64, device="cuda")
+    modes = {"fixed": (0, 0), "gstop": (1, 0), "gstop_freeze": (1, 1)}
+    points = []
+    with ClockSampler(0) as clk:
+        for eb, mi in [(e, MAX_ITER) for e in (1.0, 1.5, 2.0, 2.5, 3.0, 3.5)] + [(3.0, 40)]:
+            u, llr = B.polarbp_awgn(code, SEED + 7, 0, n_cw, eb)
+            row = {"ebn0_db": eb, "max_iter": mi, "codewords": n_cw}
+            for name, mode in modes.items():
+                B.polarbp_decode(code, llr, mi, ALPHA, *mode, uh, it, pe, stream=stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.polarbp_decode(code, llr, mi, ALPHA, *mode, uh, it, pe, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                errs = int((uh != u).any(dim=1).sum().item())
+                bit_errs = int((uh != u).sum().item())
+                pe_sum = float(pe.double().sum().item())
+                row[name] = {"fer": errs / n_cw, "fer_ci95": list(wilson(errs, n_cw)), "ber": bit_errs / (n_cw * K),
+                             "avg_iters": float(it.double().mean().item()), "pe_per_codeword": pe_sum / n_cw,
+                             "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9, "ms": ms,
+                             "alu_frac": pe_sum / (ms * 1e-3) / PEAK_PE_PER_S}
+            points.append(row)
+            del u, llr
+            torch.cuda.empty_cache()
+    line = {"metric": "FER / throughput sweep, (1024,512), Eb/N0 1.0-3.5 dB, three modes", "unit": "Gbit/s",
+            "value": next(p for p in points if p["ebn0_db"] == 3.0 and p["max_iter"] == MAX_ITER)["gstop_freeze"]["info_gbit_s"],
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"(1024,512) code, {n_cw} codewords per point, alpha {ALPHA}, device generator"},
+            "points": points, "clocks": clk.summary(), "gpu_launches": 2 * 3 * len(points)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_long(args):
     """Long codes: N in {8192, 16384, 32768}, K = N/2, Eb/N0 in {2.0, 2.5, 3.0} dB, 10^5
     codewords per point (device generator), G-matrix stop + CSFG freezing, at most 100
@@ -690,7 +747,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms"], default="n1024",
+    ap.add_argument("--sweep-codewords", type=int, default=1000000)
+    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms", "sweep"], default="n1024",
                     help="n1024: the (1024,512) headline; mixed: the mixed-length stream; long: N = 8192..32768 "
                          "on thread-block clusters; wms: learned weights")
     ap.add_argument("--long-codewords", type=int, default=100000)
@@ -708,6 +766,8 @@ def main():
         return run_wms(args)
     if args.workload == "long":
         return run_long(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 
