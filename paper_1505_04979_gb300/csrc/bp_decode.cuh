@@ -109,12 +109,17 @@ __host__ __device__ __forceinline__ constexpr int padded_off(int e)
 }
 
 // alpha * sign(x) sign(y) min(|x|, |y|)  (Eq. (1)).  The magnitude is exact,
-// the product by alpha rounds once; the sign bit is xor-ed in.
+// the product by alpha rounds once.  The sign is that of the product x * y,
+// whose IEEE sign is the xor of the operands' signs; it is computed on the FMA
+// pipe, which leaves the (half-rate) integer/logic pipe two instructions per
+// term instead of three.  The one exception, 0 * inf = NaN, only occurs when
+// the magnitude is 0, so it can change nothing but the sign of a zero result,
+// and the sign of a zero never reaches a nonzero message or a decision.
 __device__ __forceinline__ float fms(float x, float y, float alpha)
 {
     const float mag = __fmul_rn(alpha, fminf(fabsf(x), fabsf(y)));
-    const uint32_t s = (__float_as_uint(x) ^ __float_as_uint(y)) & 0x80000000u;
-    return __uint_as_float(__float_as_uint(mag) | s);
+    const float p = __fmul_rn(x, y);
+    return __uint_as_float(__float_as_uint(mag) | (__float_as_uint(p) & 0x80000000u));
 }
 
 struct DecodeArgs {
@@ -397,10 +402,24 @@ __device__ __forceinline__ void propagate(Smem<M>& sm, int P, int J, int lane)
         const int Sp = N >> jp;
         if (P & (Sp - 1)) break;
         const int bp = P - Sp;
-        uint32_t v[RW];
-        packed_load<RW>(sm.U, bp, Sp, v, lane);
-        polar_xform<RW>(v, Sp, lane);
-        packed_store<RW>(sm.Xf + jp * NW, bp, Sp, v, lane);
+        // F^{(x)k} = [[F', 0], [F', F']]: the encoding of (u_left, u_right) is
+        // (x_left ^ x_right, x_right), the halves' own encodings being their
+        // stage-(jp+1) decisions.
+        const uint32_t* xc = sm.Xf + (jp + 1) * NW;
+        uint32_t* xo = sm.Xf + jp * NW;
+        if (Sp >= 64) {
+            const int hw = Sp >> 6;
+            for (int w = lane; w < 2 * hw; w += 32) {
+                const int ww = (bp >> 5) + w;
+                xo[ww] = w < hw ? (xc[ww] ^ xc[ww + hw]) : xc[ww];
+            }
+        } else if (lane == 0) {
+            const int h = Sp >> 1, off = bp & 31;
+            const uint32_t x = xc[bp >> 5];
+            const uint32_t v = x ^ ((x >> h) & (((1u << h) - 1u) << off));
+            const uint32_t mk = low_mask(Sp) << off;
+            xo[bp >> 5] = (xo[bp >> 5] & ~mk) | (v & mk);
+        }
         note_event(sm, jp, bp, P, lane);
         __syncwarp();
     }
@@ -747,13 +766,10 @@ __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb,
     }
 }
 
-// Stage s of phase PH.  With XC > 0 the sweep is the lower M stages of a code
-// of M + XC stages (stage s here is stage s + XC there): P0 is then the covered
-// prefix within this part, stage 0 may be covered, its L column is stored, the
-// channel-side decisions are taken elsewhere and trace columns are N << XC apart.
-// One snapshot row of phase PH from each thread's 8 decisions (bit e of `byte`
-// = element e), in natural order for N >= 256.  Phase PH maps element e of
-// thread t to position (t & (2^lo - 1)) | e << lo | (t >> lo) << (lo + 3):
+// Snapshot rows: the hard decisions of one column, written by the phase PH
+// that computes it, in natural order for N >= 256 (one byte per thread for
+// smaller codes).  Phase PH maps element e of thread t to position
+// (t & (2^lo - 1)) | e << lo | (t >> lo) << (lo + 3):
 //   lo >= 5: the lanes of a warp cover 32 consecutive positions of each
 //            element, so one ballot per element is a word;
 //   lo = 4, 3: a word takes 16 (8) lanes of two (four) elements' ballots,
@@ -762,63 +778,80 @@ __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb,
 //            bit positions and or-ed across the four lanes;
 //   lo = 0: each thread's byte is 8 consecutive positions.
 template <int M, int PH>
-__device__ __forceinline__ void snap_row(uint8_t* row, uint32_t byte, int tid)
+__host__ __device__ constexpr bool ballot_row()
+{
+    return natural_rows<M>() && Geo<M>::lo(PH) >= 3;
+}
+
+// Rows of phases with lo >= 3, from the ballots b[e] of the warp's decisions on
+// element e (taken straight from the comparisons by the caller).
+template <int M, int PH>
+__device__ __forceinline__ void snap_row_b(uint8_t* row, const uint32_t (&b)[8], int tid)
 {
     constexpr int lo = Geo<M>::lo(PH);
-    if constexpr (lo == 0 || !natural_rows<M>()) {
-        row[tid] = (uint8_t)byte;
+    static_assert(ballot_row<M, PH>(), "ballot rows only");
+    uint32_t* w = reinterpret_cast<uint32_t*>(row);
+    const int lane = tid & 31, k = tid >> 5;
+    if constexpr (lo >= 5) {
+        if (lane == 0) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) w[elem_index<M, PH>(tid & ~31, e) >> 5] = b[e];
+        }
+    } else if constexpr (lo == 4) {
+        // word (e >> 1) | (2k + h) << 2 holds lanes 16h.. of elements 2(e>>1) and 2(e>>1)+1
+        if (lane < 8) {
+            const int eh = lane & 3, h = lane >> 2;
+            const uint32_t b0 = eh == 0 ? b[0] : eh == 1 ? b[2] : eh == 2 ? b[4] : b[6];
+            const uint32_t b1 = eh == 0 ? b[1] : eh == 1 ? b[3] : eh == 2 ? b[5] : b[7];
+            w[eh | ((2 * k + h) << 2)] = __byte_perm(b0, b1, h ? 0x7632u : 0x5410u);
+        }
     } else {
-        uint32_t* w = reinterpret_cast<uint32_t*>(row);
-        const int lane = tid & 31, k = tid >> 5;
-        if constexpr (lo >= 3) {
-            uint32_t b[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) b[e] = __ballot_sync(kFull, (byte >> e) & 1u);
-            if constexpr (lo >= 5) {
-                if (lane == 0) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) w[elem_index<M, PH>(tid & ~31, e) >> 5] = b[e];
-                }
-            } else if constexpr (lo == 4) {
-                // word (e >> 1) | (2k + h) << 2 holds lanes 16h.. of elements 2(e>>1) and 2(e>>1)+1
-                if (lane < 8) {
-                    const int eh = lane & 3, h = lane >> 2;
-                    const uint32_t b0 = eh == 0 ? b[0] : eh == 1 ? b[2] : eh == 2 ? b[4] : b[6];
-                    const uint32_t b1 = eh == 0 ? b[1] : eh == 1 ? b[3] : eh == 2 ? b[5] : b[7];
-                    w[eh | ((2 * k + h) << 2)] = __byte_perm(b0, b1, h ? 0x7632u : 0x5410u);
-                }
-            } else {
-                // lo = 3: word (e >> 2) | (4k + g) << 1 holds byte g of elements 4(e>>2) .. +3
-                if (lane < 8) {
-                    const int eh = lane >> 2, g = lane & 3;
-                    const uint32_t b0 = eh ? b[4] : b[0], b1 = eh ? b[5] : b[1];
-                    const uint32_t b2 = eh ? b[6] : b[2], b3 = eh ? b[7] : b[3];
-                    const uint32_t sel = (uint32_t)g | ((uint32_t)(4 + g) << 4);
-                    w[eh | ((4 * k + g) << 1)] = __byte_perm(__byte_perm(b0, b1, sel), __byte_perm(b2, b3, sel), 0x5410u);
-                }
-            }
-        } else {
-            uint32_t x = byte;
-            if constexpr (lo == 2) {
-                // bit e -> 4e + (t & 3)
-                x = (x | (x << 12)) & 0x000F000Fu;
-                x = (x | (x << 6)) & 0x03030303u;
-                x = (x | (x << 3)) & 0x11111111u;
-                x <<= (tid & 3);
-            } else {
-                // lo = 1: bit e -> 2e + (t & 1) + 16 ((t >> 1) & 1)
-                x = (x | (x << 4)) & 0x0F0Fu;
-                x = (x | (x << 2)) & 0x3333u;
-                x = (x | (x << 1)) & 0x5555u;
-                x <<= (tid & 1) + 16 * ((tid >> 1) & 1);
-            }
-            x |= __shfl_xor_sync(kFull, x, 1);
-            x |= __shfl_xor_sync(kFull, x, 2);
-            if ((tid & 3) == 0) w[tid >> 2] = x;
+        // lo = 3: word (e >> 2) | (4k + g) << 1 holds byte g of elements 4(e>>2) .. +3
+        if (lane < 8) {
+            const int eh = lane >> 2, g = lane & 3;
+            const uint32_t b0 = eh ? b[4] : b[0], b1 = eh ? b[5] : b[1];
+            const uint32_t b2 = eh ? b[6] : b[2], b3 = eh ? b[7] : b[3];
+            const uint32_t sel = (uint32_t)g | ((uint32_t)(4 + g) << 4);
+            w[eh | ((4 * k + g) << 1)] = __byte_perm(__byte_perm(b0, b1, sel), __byte_perm(b2, b3, sel), 0x5410u);
         }
     }
 }
 
+// Rows of the other phases, from each thread's byte of decisions (bit e =
+// element e).
+template <int M, int PH>
+__device__ __forceinline__ void snap_row(uint8_t* row, uint32_t byte, int tid)
+{
+    constexpr int lo = Geo<M>::lo(PH);
+    static_assert(!ballot_row<M, PH>(), "rows with lo >= 3 are built from ballots");
+    if constexpr (lo == 0 || !natural_rows<M>()) {
+        row[tid] = (uint8_t)byte;
+    } else {
+        uint32_t* w = reinterpret_cast<uint32_t*>(row);
+        uint32_t x = byte;
+        if constexpr (lo == 2) {
+            // bit e -> 4e + (t & 3)
+            x = (x | (x << 12)) & 0x000F000Fu;
+            x = (x | (x << 6)) & 0x03030303u;
+            x = (x | (x << 3)) & 0x11111111u;
+            x <<= (tid & 3);
+        } else {
+            // lo = 1: bit e -> 2e + (t & 1) + 16 ((t >> 1) & 1)
+            x = (x | (x << 4)) & 0x0F0Fu;
+            x = (x | (x << 2)) & 0x3333u;
+            x = (x | (x << 1)) & 0x5555u;
+            x <<= (tid & 1) + 16 * ((tid >> 1) & 1);
+        }
+        x |= __shfl_xor_sync(kFull, x, 1);
+        x |= __shfl_xor_sync(kFull, x, 2);
+        if ((tid & 3) == 0) w[tid >> 2] = x;
+    }
+}
+
+// Stage s of phase PH.  With XC > 0 the sweep is the lower M stages of a code
+// of M + XC stages (stage s here is stage s + XC there): P0 is then the covered
+// prefix within this part, stage 0 may be covered, its L column is stored, the
+// channel-side decisions are taken elsewhere and trace columns are N << XC apart.
 template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE, int XC = 0>
 __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha, const CwIO& a,
                                           long long trace_base)
@@ -832,6 +865,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     constexpr long long TSTRIDE = (long long)N << XC;
     const int thr = (s + XC == 0 || !FREEZE) ? 0 : ((P0 >> (M - s)) << (M - s));
     uint32_t xbyte = 0;  // stage 0: decisions on R[0] + L[0] (G-matrix stop)
+    uint32_t xb[8];      // the same as ballots, for rows built from ballots
     // padded bases for the boundary columns read (s+1) and written (s) here
     const int pb_in = G::is_boundary(s + 1) ? padded_base<M, PH, G::padsh(G::bslot(s + 1))>(tid) : 0;
     const int pb_out = G::is_boundary(s) ? padded_base<M, PH, G::padsh(G::bslot(s))>(tid) : (s == 0 ? tid : 0);
@@ -855,8 +889,13 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         store_L<M, PH, s, XC>(rg, sm, e, pb_out, nLa, covered);
         store_L<M, PH, s, XC>(rg, sm, e2, pb_out, nLb, covered);
         if constexpr (s == 0 && GSTOP && XC == 0) {
-            xbyte |= (__fadd_rn(Ra, nLa) < 0.f ? 1u : 0u) << e;
-            xbyte |= (__fadd_rn(Rb, nLb) < 0.f ? 1u : 0u) << e2;
+            if constexpr (ballot_row<M, PH>()) {
+                xb[e] = __ballot_sync(kFull, __fadd_rn(Ra, nLa) < 0.f);
+                xb[e2] = __ballot_sync(kFull, __fadd_rn(Rb, nLb) < 0.f);
+            } else {
+                xbyte |= (__fadd_rn(Ra, nLa) < 0.f ? 1u : 0u) << e;
+                xbyte |= (__fadd_rn(Rb, nLb) < 0.f ? 1u : 0u) << e2;
+            }
         }
         if constexpr (s == 0 && TRACE && XC == 0) {
             a.trace_L[trace_base + ia] = nLa;
@@ -865,12 +904,22 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         rg.R[e] = nRa;
         rg.R[e2] = nRb;
     }
-    if constexpr (s == 0 && GSTOP && XC == 0) snap_row<M, PH>(sm.hd, xbyte, tid);
+    if constexpr (s == 0 && GSTOP && XC == 0) {
+        if constexpr (ballot_row<M, PH>()) snap_row_b<M, PH>(sm.hd, xb, tid);
+        else snap_row<M, PH>(sm.hd, xbyte, tid);
+    }
     if constexpr (snap) {
-        uint32_t byte = 0;
+        if constexpr (ballot_row<M, PH>()) {
+            uint32_t b[8];
 #pragma unroll
-        for (int e = 0; e < EL; ++e) byte |= (rg.R[e] < 0.f ? 1u : 0u) << e;
-        snap_row<M, PH>(sm.hd + (s + 1) * G::HDS, byte, tid);
+            for (int e = 0; e < 8; ++e) b[e] = __ballot_sync(kFull, rg.R[e] < 0.f);
+            snap_row_b<M, PH>(sm.hd + (s + 1) * G::HDS, b, tid);
+        } else {
+            uint32_t byte = 0;
+#pragma unroll
+            for (int e = 0; e < EL; ++e) byte |= (rg.R[e] < 0.f ? 1u : 0u) << e;
+            snap_row<M, PH>(sm.hd + (s + 1) * G::HDS, byte, tid);
+        }
     }
     if constexpr (TRACE) {
 #pragma unroll
