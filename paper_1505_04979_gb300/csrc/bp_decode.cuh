@@ -446,28 +446,57 @@ struct Spec {
     int fail;             // bit j: the speculative check of stage j fails Eq. (4)
 };
 
-template <int M, bool SMALL = true>
-__device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int jmin, int lane)
+// Lane-constant part of the speculative check: the stage and word of each of
+// the lane's slots, and which of the cross-word butterfly steps apply to it.
+template <int M>
+struct SpecSlots {
+    int lvl[Spec<M>::R];
+    int w[Spec<M>::R];
+    unsigned xm[Spec<M>::R];  // bit q: step d = 2^q xors in the partner word
+};
+
+template <int M>
+__device__ __forceinline__ void spec_slots(SpecSlots<M>& ss, int lane)
 {
     using SP = Spec<M>;
     constexpr int N = 1 << M;
-    constexpr int HDS = Geo<M>::HDS;
+#pragma unroll
+    for (int r = 0; r < SP::R; ++r) {
+        const int sl = 32 * r + lane;
+        ss.lvl[r] = 0;
+        ss.w[r] = 0;
+        ss.xm[r] = 0u;
+        if (sl < SP::TW) {
+            const int lw = 31 - __clz(N / 32 - sl - 1);  // log2 of the stage's word count
+            const int wi = sl - (N / 32 - (2 << lw));
+            ss.lvl[r] = M - 5 - lw;
+            ss.w[r] = wi;
+            const int W = 1 << lw;
+#pragma unroll
+            for (int q = 0; (1 << q) < N / 64; ++q)
+                if (W > (1 << q) && !(wi & (1 << q))) ss.xm[r] |= 1u << q;
+        }
+    }
+}
+
+template <int M, bool SMALL = true>
+__device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, const SpecSlots<M>& ss, int P0, int jmin, int lane)
+{
+    using SP = Spec<M>;
+    constexpr int N = 1 << M;
     unsigned bad_levels = 0;
     if constexpr (SP::TW > 0) if (jmin <= SP::JB) {
+        int base[SP::R];
 #pragma unroll
         for (int r = 0; r < SP::R; ++r) {
-            const int sl = 32 * r + lane;
-            sp.lvl[r] = 0;
-            sp.w[r] = 0;
+            sp.lvl[r] = ss.lvl[r];
+            sp.w[r] = ss.w[r];
             sp.x[r] = 0u;
-            if (sl < SP::TW) {
-                const int lw = 31 - __clz(N / 32 - sl - 1);  // log2 of the stage's word count
-                const int j = M - 5 - lw;
-                const int wi = sl - (N / 32 - (2 << lw));
-                const int base = (P0 >> (M - j)) << (M - j);
-                sp.lvl[r] = j;
-                sp.w[r] = wi;
-                sp.x[r] = snap_word<M>(sm.hd, j, base + 32 * wi);
+            base[r] = 0;
+            if (ss.lvl[r]) {
+                const int j = ss.lvl[r];
+                base[r] = (P0 >> (M - j)) << (M - j);
+                sp.x[r] = snap_word<M>(sm.hd, j, base[r] + 32 * ss.w[r]);
             }
             uint32_t v = sp.x[r];
 #pragma unroll
@@ -475,32 +504,27 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, int P0, int 
             sp.u[r] = v;
         }
 #pragma unroll
-        for (int d = 1; d < N / 64; d <<= 1) {
+        for (int q = 0; (1 << q) < N / 64; ++q) {
+            const int d = 1 << q;
             if (d < 32) {
 #pragma unroll
                 for (int r = 0; r < SP::R; ++r) {
                     const uint32_t y = __shfl_xor_sync(kFull, sp.u[r], d);
-                    const int W = sp.lvl[r] ? (N >> (sp.lvl[r] + 5)) : 0;
-                    if (W > d && !(sp.w[r] & d)) sp.u[r] ^= y;
+                    if (ss.xm[r] & (1u << q)) sp.u[r] ^= y;
                 }
             } else {
                 const int dr = d / 32;
 #pragma unroll
                 for (int r = 0; r < SP::R; ++r) {
                     if ((r & dr) || r + dr >= SP::R) continue;
-                    const int W = sp.lvl[r] ? (N >> (sp.lvl[r] + 5)) : 0;
-                    if (W > d && !(sp.w[r] & d)) sp.u[r] ^= sp.u[r + dr];
+                    if (ss.xm[r] & (1u << q)) sp.u[r] ^= sp.u[r + dr];
                 }
             }
         }
 #pragma unroll
         for (int r = 0; r < SP::R; ++r) {
             unsigned flag = 0;
-            if (sp.lvl[r]) {
-                const int j = sp.lvl[r];
-                const int base = (P0 >> (M - j)) << (M - j);
-                if (sp.u[r] & sm.Fz[(base >> 5) + sp.w[r]]) flag = 1u << j;
-            }
+            if (ss.lvl[r] && (sp.u[r] & sm.Fz[(base[r] >> 5) + ss.w[r]])) flag = 1u << ss.lvl[r];
             bad_levels |= __reduce_or_sync(kFull, flag);
         }
     }
@@ -540,10 +564,12 @@ __device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
     constexpr int N = Geo<M>::N, NW = Geo<M>::NW;
     int jmin = 1;
     int Ps = P;  // lane s (1 <= s < M): P seen by stage s, i.e. after the last commit at a stage <= s
+    SpecSlots<M> ss;
+    spec_slots<M>(ss, lane);
 #pragma unroll 1
     while (P < N && jmin <= M) {
         Spec<M> sp;
-        speculate<M>(sm, sp, P, jmin, lane);
+        speculate<M>(sm, sp, ss, P, jmin, lane);
         const unsigned wanted = ((2u << M) - 1u) & ~((1u << jmin) - 1u);
         const unsigned pass = ~(unsigned)sp.fail & wanted;
         if (!pass) break;
