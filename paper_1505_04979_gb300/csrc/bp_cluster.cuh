@@ -346,14 +346,16 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
         }
         if (!finite) atomicOr(a.status, 1u);
 #pragma unroll
-        for (int c = 0; c < GL::NR; ++c)
+        for (int c = 0; c < GL::NRA; ++c)
 #pragma unroll
             for (int e = 0; e < EL; ++e) rg.Lr[c][e] = 0.f;
         __syncthreads();
-        // source-side prior: +inf on frozen positions, 0 elsewhere
+        // source-side prior: +inf on frozen positions, 0 elsewhere (column 12 is in shared memory)
 #pragma unroll
-        for (int e = 0; e < EL; ++e)
-            rg.Lr[GL::rslot(12)][e] = bit_of(sm.Fz, elem_index<12, GL::NP - 1>(tid, e)) ? INFINITY : 0.f;
+        for (int e = 0; e < EL; ++e) {
+            const int i = elem_index<12, GL::NP - 1>(tid, e);
+            sm.Lm[i] = bit_of(sm.Fz, i) ? INFINITY : 0.f;
+        }
     }
     cl.sync();  // every block of the cluster has started and initialised
 

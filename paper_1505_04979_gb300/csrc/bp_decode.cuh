@@ -48,12 +48,19 @@ struct Geo {
     static constexpr int NW = N < 32 ? 1 : N / 32;  // 32-bit words of an N-bit vector
     static constexpr int NB = (M - 1) / 3;          // shared-memory L columns
     static constexpr int MIN_BLOCKS = (640 / BLOCK) < 1 ? 1 : (640 / BLOCK);
+    // Blocks per SM the kernels are compiled for (the register bound is 65536 / (blocks x BLOCK)).
+    // The freezing kernels spend much of an iteration in one warp (the CSFG walk), so more
+    // resident blocks hide more of it: at N = 1024 six blocks of 128 threads (80 registers, no
+    // spills) measured 4-6 % faster than five.  At N = 256..2048 otherwise, and for the kernels
+    // without freezing, the 640-thread bound measured as fast or faster.
+    __host__ __device__ static constexpr int min_blocks(bool freeze) { return (freeze && M == 10) ? 6 : MIN_BLOCKS; }
 
     __host__ __device__ static constexpr int s0(int p) { return 3 * p; }
     __host__ __device__ static constexpr int cnt(int p) { return (M - 3 * p) < 3 ? (M - 3 * p) : 3; }
     __host__ __device__ static constexpr int lo(int p) { return (p == NP - 1) ? 0 : (M - 3 - 3 * p); }
     __host__ __device__ static constexpr bool is_boundary(int c) { return c > 0 && c < M && (c % 3) == 0; }
-    __host__ __device__ static constexpr bool is_reg(int c) { return c > 0 && c <= M && !is_boundary(c); }
+    // column M (the source side) lives in shared memory, see Smem::Lm
+    __host__ __device__ static constexpr bool is_reg(int c) { return c > 0 && c < M && !is_boundary(c); }
     __host__ __device__ static constexpr int bslot(int c) { return c / 3 - 1; }
     __host__ __device__ static constexpr int rslot(int c)
     {
@@ -61,7 +68,8 @@ struct Geo {
         for (int x = 1; x < c; ++x) r += is_reg(x) ? 1 : 0;
         return r;
     }
-    static constexpr int NR = M - NB;  // register columns
+    static constexpr int NR = M - NB - 1;          // register columns (1..M-1 less the boundaries)
+    static constexpr int NRA = NR > 0 ? NR : 1;    // their array extent
     // Shared-memory layout of the buffers at the boundary between phases b and
     // b+1: entry i sits at i + (i >> padsh(b)).  The shift minimises bank
     // conflicts of the two phases' access patterns (found by enumerating them);
@@ -182,7 +190,9 @@ struct SmemLayout {
     static constexpr size_t hd_bytes = (size_t)(M + 1) * G::HDS;
     // two NW-word buffers for the encoding of the channel-side decisions
     static constexpr size_t off_Ge = (off_Hd + hd_bytes + 15) / 16 * 16;
-    static constexpr size_t bytes = (off_Ge + 2 * sizeof(uint32_t) * NW + 15) / 16 * 16;
+    // column M in natural order; 32-byte aligned so each thread's 8 entries load as two float4
+    static constexpr size_t off_Lm = (off_Ge + 2 * sizeof(uint32_t) * NW + 31) / 32 * 32;
+    static constexpr size_t bytes = (off_Lm + sizeof(float) * N + 15) / 16 * 16;
 };
 
 template <int M>
@@ -197,11 +207,13 @@ struct Smem {
     uint8_t* hd;    // [(M+1)][HDS] hard-decision snapshots (one byte per thread)
     float* L0;      // column 0 of a sweep that is the lower part of a larger code (else unused)
     uint32_t* Ge;   // [2][NW] encoding of HD(R[0] + L[0]), built during the sweep
+    float* Lm;      // [N] column M: the prior (+inf frozen, 0 otherwise) and the stage-M feedback
     __device__ __forceinline__ explicit Smem(unsigned char* base)
     {
         L0 = nullptr;
         using L = SmemLayout<M>;
         Ge = reinterpret_cast<uint32_t*>(base + L::off_Ge);
+        Lm = reinterpret_cast<float*>(base + L::off_Lm);
         Lb = reinterpret_cast<float*>(base + L::off_Lb);
         Rx = reinterpret_cast<float*>(base + L::off_Rx);
         llr = reinterpret_cast<float*>(base + L::off_Llr);
@@ -590,8 +602,10 @@ __device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
             uint32_t* px = sm.Xf + J * NW + (cand >> 5);
             *pu = (*pu & ~mk) | ((sp.us << (cand & 31)) & mk);
             *px = (*px & ~mk) | ((sp.xs << (cand & 31)) & mk);
+            // a stage-M CSFG is one position; its feedback goes straight to column M
+            if (J == M) sm.Lm[cand] = (sp.xs & 1u) ? -INFINITY : INFINITY;
         }
-        note_event(sm, J, cand, cand + S, lane);
+        if (J < M) note_event(sm, J, cand, cand + S, lane);
         P = cand + S;
         __syncwarp();
         propagate<M>(sm, P, J, lane);
@@ -749,7 +763,7 @@ __device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
 template <int M>
 struct Regs {
     float R[Geo<M>::EL];
-    float Lr[Geo<M>::NR][Geo<M>::EL];
+    float Lr[Geo<M>::NRA][Geo<M>::EL];
 };
 
 // L of column C at element e of the running phase PH.  Boundary column C is
@@ -762,6 +776,7 @@ __device__ __forceinline__ float load_L(Regs<M>& rg, Smem<M>& sm, int e, int pb)
         constexpr int SH = G::padsh(G::bslot(C));
         return sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)];
     } else {
+        static_assert(C < M, "column M is read from shared memory by run_stage");
         return rg.Lr[G::rslot(C)][e];
     }
 }
@@ -894,6 +909,22 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     uint32_t xb[8];      // the same as ballots, for rows built from ballots
     // padded bases for the boundary columns read (s+1) and written (s) here
     const int pb_in = G::is_boundary(s + 1) ? padded_base<M, PH, G::padsh(G::bslot(s + 1))>(tid) : 0;
+    // column M: this thread's entries, which the last phase (register bits from bit 0) holds
+    // at consecutive positions
+    float lm[EL];
+    if constexpr (s + 1 == M) {
+        static_assert(G::lo(PH) == 0, "stage M-1 runs in the last phase");
+        const int i0 = elem_index<M, PH>(tid, 0);
+        if constexpr (EL == 8) {
+            const float4 q0 = reinterpret_cast<const float4*>(sm.Lm + i0)[0];
+            const float4 q1 = reinterpret_cast<const float4*>(sm.Lm + i0)[1];
+            lm[0] = q0.x; lm[1] = q0.y; lm[2] = q0.z; lm[3] = q0.w;
+            lm[4] = q1.x; lm[5] = q1.y; lm[6] = q1.z; lm[7] = q1.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) lm[e] = sm.Lm[i0 + e];
+        }
+    }
     const int pb_out = G::is_boundary(s) ? padded_base<M, PH, G::padsh(G::bslot(s))>(tid) : (s == 0 ? tid : 0);
 #pragma unroll
     for (int e = 0; e < EL; ++e) {
@@ -902,8 +933,14 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         const int ia = elem_index<M, PH>(tid, e);
         const int ib = ia + (1 << b);
         const bool covered = FREEZE && s + XC > 0 && ia < thr;  // PE inside a covered CSFG
-        const float La = load_L<M, PH, s + 1>(rg, sm, e, pb_in);
-        const float Lb = load_L<M, PH, s + 1>(rg, sm, e2, pb_in);
+        float La, Lb;
+        if constexpr (s + 1 == M) {
+            La = lm[e];
+            Lb = lm[e2];
+        } else {
+            La = load_L<M, PH, s + 1>(rg, sm, e, pb_in);
+            Lb = load_L<M, PH, s + 1>(rg, sm, e2, pb_in);
+        }
         const float Ra = rg.R[e];
         const float Rb = rg.R[e2];
         const float t = __fadd_rn(Lb, Rb);
@@ -940,6 +977,18 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
 #pragma unroll
             for (int e = 0; e < 8; ++e) b[e] = __ballot_sync(kFull, rg.R[e] < 0.f);
             snap_row_b<M, PH>(sm.hd + (s + 1) * G::HDS, b, tid);
+        } else if constexpr (natural_rows<M>() && (G::lo(PH) == 1 || G::lo(PH) == 2)) {
+            // the decisions spread straight to their bits in the natural-order word
+            // that four consecutive threads share (see snap_row)
+            constexpr int LO = G::lo(PH);
+            uint32_t x = 0;
+#pragma unroll
+            for (int e = 0; e < EL; ++e) x |= (rg.R[e] < 0.f ? 1u : 0u) << (e << LO);
+            if constexpr (LO == 2) x <<= (tid & 3);
+            else x <<= (tid & 1) + 16 * ((tid >> 1) & 1);
+            x |= __shfl_xor_sync(kFull, x, 1);
+            x |= __shfl_xor_sync(kFull, x, 2);
+            if ((tid & 3) == 0) reinterpret_cast<uint32_t*>(sm.hd + (s + 1) * G::HDS)[tid >> 2] = x;
         } else {
             uint32_t byte = 0;
 #pragma unroll
@@ -998,14 +1047,41 @@ __device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, 
             const uint32_t* xf = sm.Xf + C * G::NW;
             constexpr int PH = G::is_boundary(C) ? (C - 1) / 3 : G::owner(C);
             constexpr int SH = G::is_boundary(C) ? G::padsh(G::bslot(C)) : 5;
-            const int pb = padded_base<M, PH, SH>(tid);
+            // element e of this thread sits at i0 + (e << LO); elements [e1, e2) lie in [lo, hi)
+            constexpr int LO = G::lo(PH);
+            const int i0 = elem_index<M, PH>(tid, 0);
+            const int e1 = min(G::EL, max(0, (lo - i0 + (1 << LO) - 1) >> LO));
+            const int e2 = min(G::EL, max(0, (hi - i0 + (1 << LO) - 1) >> LO));
+            if (e1 < e2) {
+                // the thread's decisions, bit e for element e: its positions lie in one aligned
+                // segment of 8 << LO positions, i.e. in one word for LO <= 2
+                uint32_t bits = 0;
+                if constexpr (LO >= 5) {
 #pragma unroll
-            for (int e = 0; e < G::EL; ++e) {
-                const int i = elem_index<M, PH>(tid, e);
-                if (i >= lo && i < hi) {
-                    const float v = bit_of(xf, i) ? -INFINITY : INFINITY;
-                    if constexpr (G::is_boundary(C)) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
-                    else rg.Lr[G::rslot(C)][e] = v;
+                    for (int e = 0; e < G::EL; ++e)
+                        if (e >= e1 && e < e2) bits |= ((xf[(i0 >> 5) + (e << (LO - 5))] >> (i0 & 31)) & 1u) << e;
+                } else if constexpr (LO <= 2) {
+                    const uint32_t w = xf[i0 >> 5] >> (i0 & 31);
+#pragma unroll
+                    for (int e = 0; e < G::EL; ++e) bits |= ((w >> (e << LO)) & 1u) << e;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < (G::EL << LO) / 32; ++q) {
+                        const uint32_t w = xf[(i0 >> 5) + q] >> (i0 & 31);
+#pragma unroll
+                        for (int e = 0; e < G::EL; ++e)
+                            if (((e << LO) >> 5) == q) bits |= ((w >> ((e << LO) & 31)) & 1u) << e;
+                    }
+                }
+                const int pb = padded_base<M, PH, SH>(tid);
+#pragma unroll
+                for (int e = 0; e < G::EL; ++e) {
+                    if (e >= e1 && e < e2) {
+                        const float v = ((bits >> e) & 1u) ? -INFINITY : INFINITY;
+                        if constexpr (C == M) sm.Lm[i0 + (e << LO)] = v;
+                        else if constexpr (G::is_boundary(C)) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
+                        else rg.Lr[G::rslot(C)][e] = v;
+                    }
                 }
             }
         }
@@ -1020,7 +1096,9 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
     using G = Geo<M>;
     constexpr long long TSTRIDE = (long long)G::N << XC;
     if constexpr (C <= M) {
-        if constexpr (G::is_boundary(C)) {
+        if constexpr (C == M) {
+            for (int i = tid; i < G::N; i += G::BLOCK) a.trace_L[trace_base + C * TSTRIDE + i] = sm.Lm[i];
+        } else if constexpr (G::is_boundary(C)) {
             constexpr int SH = G::padsh(G::bslot(C));
             for (int i = tid; i < G::N; i += G::BLOCK)
                 a.trace_L[trace_base + C * TSTRIDE + i] = sm.Lb[G::bslot(C) * G::BUF + padded<SH>(i)];
@@ -1050,6 +1128,8 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
         sm.U[w] = 0u;
     }
     for (int i = tid; i < G::NB * G::BUF; i += G::BLOCK) sm.Lb[i] = 0.f;
+    // source-side prior (reading: +inf on frozen positions, 0 elsewhere)
+    for (int i = tid; i < N; i += G::BLOCK) sm.Lm[i] = ((a.frozen_words[i >> 5] >> (i & 31)) & 1u) ? INFINITY : 0.f;
     {
         uint32_t* hd32 = reinterpret_cast<uint32_t*>(sm.hd);
         for (int i = tid; i < (int)(SmemLayout<M>::hd_bytes / 4); i += G::BLOCK) hd32[i] = 0u;
@@ -1073,15 +1153,9 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
         }
         if (!finite) atomicOr(status, 1u);
 #pragma unroll
-        for (int c = 0; c < G::NR; ++c)
+        for (int c = 0; c < G::NRA; ++c)
 #pragma unroll
             for (int e = 0; e < EL; ++e) rg.Lr[c][e] = 0.f;
-        // source-side prior (reading: +inf on frozen positions, 0 elsewhere)
-#pragma unroll
-        for (int e = 0; e < EL; ++e) {
-            const int i = elem_index<M, G::NP - 1>(tid, e);
-            rg.Lr[G::rslot(M)][e] = bit_of(sm.Fz, i) ? INFINITY : 0.f;
-        }
     }
 
     int it = 1;
@@ -1145,7 +1219,7 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
 
 // One codeword per block, grid = batch.
 template <int M, bool GSTOP, bool FREEZE, bool TRACE>
-__global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::MIN_BLOCKS) bp_decode_kernel(DecodeArgs a)
+__global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::min_blocks(FREEZE)) bp_decode_kernel(DecodeArgs a)
 {
     constexpr int N = Geo<M>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1186,10 +1260,12 @@ template <int M, int CPC>
 struct PersistentShape {
     static constexpr int THREADS = Geo<M>::BLOCK * CPC;
     static constexpr int MIN_BLOCKS = (640 / THREADS) < 1 ? 1 : (640 / THREADS);
+    // one codeword per block: the bound of bp_decode_kernel
+    static constexpr int min_blocks(bool freeze) { return CPC == 1 ? Geo<M>::min_blocks(freeze) : MIN_BLOCKS; }
 };
 
 template <int M, bool GSTOP, bool FREEZE, int CPC>
-__global__ void __launch_bounds__(PersistentShape<M, CPC>::THREADS, PersistentShape<M, CPC>::MIN_BLOCKS)
+__global__ void __launch_bounds__(PersistentShape<M, CPC>::THREADS, PersistentShape<M, CPC>::min_blocks(FREEZE))
     bp_decode_persistent(SegArgs a)
 {
     using G = Geo<M>;
