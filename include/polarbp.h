@@ -64,7 +64,9 @@ typedef struct polarbp_code polarbp_code;
  *                construction).  When given, its popcount must be N-K.
  *   z0           erasure probability in (0, 1); ignored when frozen_mask != NULL.
  *   out          receives the handle.
- * Allocates the handle and a few KB of device memory on the current device.
+ * Allocates the handle and a few KB of device memory on the current device,
+ * and creates three non-blocking CUDA streams and four events there for
+ * polarbp_decode_host's pipeline.
  * Errors: POLARBP_ERR_ARG, POLARBP_ERR_NOMEM, POLARBP_ERR_CUDA.
  */
 int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polarbp_code** out);
@@ -78,7 +80,7 @@ int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polar
 int polarbp_frozen_set(int N, int K, double z0, uint8_t* frozen_mask);
 
 /* polarbp_destroy -- release a handle (NULL is ignored).  Synchronises the
- * device before freeing its tables. */
+ * device before freeing its tables, streams and events. */
 void polarbp_destroy(polarbp_code* code);
 
 /* polarbp_code_info -- N, K and m = log2 N of a handle (any out pointer may be NULL). */
@@ -159,10 +161,20 @@ size_t polarbp_decode_host_workspace(const polarbp_code* code, int batch);
  * the device workspace, decodes as polarbp_decode, copies u_hat, iterations
  * and pe_updates back, and synchronises `stream` before returning.
  *   llr, u_hat, iterations, pe_updates  host arrays with the layouts above
- *                                       (iterations / pe_updates may be NULL).
+ *                                       (iterations / pe_updates may be NULL);
+ *                                       page-locked (pinned) memory lets the
+ *                                       copies overlap the decode.
  *   workspace        device buffer of at least
  *                    polarbp_decode_host_workspace(code, batch) bytes.
- * The library allocates nothing.  Errors as polarbp_decode.
+ * A batch of at least two chunks of 64 MiB of LLRs (32,768 codewords at
+ * N = 1024) runs as a pipeline on the handle's three streams: each chunk is
+ * uploaded, decoded and downloaded on one of them, so copies in both
+ * directions overlap the decode of other chunks.  The streams start after the
+ * work already queued on `stream`, and `stream` waits for them before the
+ * call synchronises it.  Host threads that share a handle are serialised
+ * while they queue a pipeline.  Smaller batches run as one upload, decode and
+ * download on `stream`.  Results do not depend on the path.
+ * The call allocates nothing.  Errors as polarbp_decode.
  */
 int polarbp_decode_host(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
                         int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,

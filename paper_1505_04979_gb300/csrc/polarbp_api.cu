@@ -3,9 +3,9 @@
 // dispatch of the decode kernels in bp_decode.cuh.
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -15,6 +15,8 @@
 #include "polarbp.h"
 #include "bp_decode.cuh"
 
+constexpr int kPipe = 3;  // streams of polarbp_decode_host's copy/decode pipeline
+
 struct polarbp_code {
     int N = 0, K = 0, m = 0;
     int device = 0;
@@ -22,6 +24,12 @@ struct polarbp_code {
     uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
     unsigned int* d_status = nullptr;
     int cpc = 1;  // codewords per block of the persistent launch
+    // polarbp_decode_host's pipeline, created with the handle so that the call
+    // itself creates nothing; `pipe_lock` serialises enqueueing on them
+    cudaStream_t pipe[kPipe] = {};
+    cudaEvent_t pipe_start = nullptr;
+    cudaEvent_t pipe_done[kPipe] = {};
+    mutable std::mutex pipe_lock;
 };
 
 // decode kernels, one translation unit per code length (compiled in parallel)
@@ -359,6 +367,19 @@ int cuda_fail(cudaError_t e, const char* what) { return ::cuda_fail(e, what); }
 int check_device(const polarbp_code* c) { return ::check_device(c); }
 }  // namespace polarbp_internal
 
+// Free everything a code handle owns (any member may still be unset).
+static void release(polarbp_code* c)
+{
+    if (c->d_frozen) cudaFree(c->d_frozen);
+    if (c->d_status) cudaFree(c->d_status);
+    for (int i = 0; i < kPipe; ++i) {
+        if (c->pipe[i]) cudaStreamDestroy(c->pipe[i]);
+        if (c->pipe_done[i]) cudaEventDestroy(c->pipe_done[i]);
+    }
+    if (c->pipe_start) cudaEventDestroy(c->pipe_start);
+    delete c;
+}
+
 extern "C" {
 
 int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polarbp_code** out)
@@ -403,12 +424,15 @@ int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polar
     if (e == cudaSuccess) e = cudaMemcpy(c->d_frozen, words.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned int));
+    for (int i = 0; i < kPipe && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&c->pipe[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->pipe_done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->pipe_start, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         int rc = (e == cudaErrorMemoryAllocation) ? fail(POLARBP_ERR_NOMEM, "device allocation failed")
                                                   : cuda_fail(e, "construct");
-        if (c->d_frozen) cudaFree(c->d_frozen);
-        if (c->d_status) cudaFree(c->d_status);
-        delete c;
+        release(c);
         return rc;
     }
     *out = c;
@@ -432,9 +456,7 @@ void polarbp_destroy(polarbp_code* c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
-    if (c->d_frozen) cudaFree(c->d_frozen);
-    if (c->d_status) cudaFree(c->d_status);
-    delete c;
+    release(c);
 }
 
 int polarbp_code_info(const polarbp_code* c, int* N, int* K, int* m)
@@ -505,18 +527,49 @@ int polarbp_decode_host(const polarbp_code* c, const float* llr, int batch, int 
     uint8_t* d_u = reinterpret_cast<uint8_t*>(ws + h.u_hat);
     int32_t* d_it = reinterpret_cast<int32_t*>(ws + h.iters);
     int64_t* d_pe = reinterpret_cast<int64_t*>(ws + h.pe);
-    const size_t nllr = (size_t)batch * c->N;
-    cudaError_t e = cudaMemcpyAsync(d_llr, llr, nllr * sizeof(float), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "llr upload");
-    int rc = decode_impl(c, d_llr, batch, max_iter, scale, stop_mode, freeze_mode, d_u, d_it, d_pe, nullptr, nullptr,
-                         nullptr, false, stream);
-    if (rc != POLARBP_OK) return rc;
-    e = cudaMemcpyAsync(u_hat, d_u, nllr, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && iterations)
-        e = cudaMemcpyAsync(iterations, d_it, (size_t)batch * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && pe_updates)
-        e = cudaMemcpyAsync(pe_updates, d_pe, (size_t)batch * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // Codewords are independent, so a large batch runs as a pipeline of chunks
+    // of about 64 MiB of LLRs, dealt round-robin to the handle's streams: the
+    // upload of one chunk, the decode of another and the download of a third
+    // overlap (the copy engines and the SMs work at once).  A batch of fewer
+    // than two chunks runs as one upload, decode and download on `stream`.
+    const int N = c->N;
+    const int cb = (int)std::max<size_t>(1, ((size_t)64 << 20) / ((size_t)N * sizeof(float)));
+    const bool piped = batch >= 2 * cb;
+    std::unique_lock<std::mutex> lock(c->pipe_lock, std::defer_lock);
+    cudaError_t e = cudaSuccess;
+    if (piped) {
+        int rc = check_device(c);
+        if (rc != POLARBP_OK) return rc;
+        lock.lock();
+        e = cudaEventRecord(c->pipe_start, s);
+        for (int i = 0; i < kPipe && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->pipe[i], c->pipe_start, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "decode_host pipeline");
+    }
+    for (int k = 0, off = 0; off < batch; ++k, off += (piped ? cb : batch)) {
+        const int nb = piped ? std::min(cb, batch - off) : batch;
+        cudaStream_t st = piped ? c->pipe[k % kPipe] : s;
+        const size_t o = (size_t)off * N, n = (size_t)nb * N;
+        e = cudaMemcpyAsync(d_llr + o, llr + o, n * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "llr upload");
+        int rc = decode_impl(c, d_llr + o, nb, max_iter, scale, stop_mode, freeze_mode, d_u + o, d_it + off, d_pe + off,
+                             nullptr, nullptr, nullptr, false, st);
+        if (rc != POLARBP_OK) return rc;
+        e = cudaMemcpyAsync(u_hat + o, d_u + o, n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && iterations)
+            e = cudaMemcpyAsync(iterations + off, d_it + off, (size_t)nb * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && pe_updates)
+            e = cudaMemcpyAsync(pe_updates + off, d_pe + off, (size_t)nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "decode_host copies");
+    }
+    if (piped) {
+        for (int i = 0; i < kPipe && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(c->pipe_done[i], c->pipe[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->pipe_done[i], 0);
+        }
+        lock.unlock();
+        if (e != cudaSuccess) return cuda_fail(e, "decode_host pipeline");
+    }
+    e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "decode_host copies");
     return POLARBP_OK;
 }

@@ -294,6 +294,33 @@ def test_host_entry_point_matches_device_entry_point(B):
     assert np.array_equal(h_u.numpy(), uh) and np.array_equal(h_it.numpy(), it) and np.array_equal(h_pe.numpy(), pe)
 
 
+def test_host_entry_point_pipelined(B):
+    """A batch of more than two chunks of 64 MiB of LLRs runs as the copy/decode pipeline on the
+    handle's streams, with a ragged last chunk; the results equal the device entry point's on the
+    same LLRs, with and without the iteration and PE-count outputs, and repeat on a second call."""
+    N, K = 1024, 512
+    cb = (64 << 20) // (4 * N)
+    batch = 2 * cb + 1234
+    code = B.polarbp_construct(N, K)
+    _, llr = B.polarbp_awgn(code, 17, 0, batch, 2.5, with_u=False)
+    uh, it, pe = B.polarbp_decode(code, llr, 60, ALPHA, 1, 1)
+    torch.cuda.synchronize()
+    ws = torch.empty(B.polarbp_decode_host_workspace(code, batch), dtype=torch.uint8, device="cuda")
+    h_llr = llr.cpu().pin_memory()
+    h_u = torch.empty((batch, N), dtype=torch.uint8).pin_memory()
+    h_it = torch.empty(batch, dtype=torch.int32).pin_memory()
+    h_pe = torch.empty(batch, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        h_u.fill_(7)
+        h_it.fill_(-1)
+        h_pe.fill_(-1)
+        B.polarbp_decode_host(code, h_llr, 60, ALPHA, 1, 1, h_u, h_it, h_pe, ws)
+        assert torch.equal(h_u, uh.cpu()) and torch.equal(h_it, it.cpu()) and torch.equal(h_pe, pe.cpu())
+    h_u.fill_(7)
+    B.polarbp_decode_host(code, h_llr, 60, ALPHA, 1, 1, h_u, None, None, ws)
+    assert torch.equal(h_u, uh.cpu())
+
+
 def test_full_size_launch_sampled(B):
     """The benchmark's launch: (1024,512), 2^20 codewords in one launch, G-matrix stop and
     freezing, 60 iterations.  Bulk inputs come from the device generator; 64 rows at
