@@ -61,11 +61,14 @@ def _load():
                                    f64p, f64p, i32p, i64p]
         lib.orc_decode_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, ci, u8p, i32p, i64p,
                                          f64p]
+        lib.orc_decode_flood.argtypes = [ci, u8p, f32p, ci, cd, ci, ci, u8p, i32p, i64p, f64p, f64p, f64p]
+        lib.orc_decode_flood_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, u8p, i32p, i64p, f64p]
         lib.orc_max_threads.argtypes = []
         lib.orc_wms_forward.argtypes = [ci, u8p, f32p, ci, f64p, ci, f64p, f64p, f64p]
         lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, f64p, f64p]
         for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
-                   "orc_decode_batch", "orc_max_threads", "orc_wms_forward", "orc_wms_backward"):
+                   "orc_decode_batch", "orc_decode_flood", "orc_decode_flood_batch", "orc_max_threads",
+                   "orc_wms_forward", "orc_wms_backward"):
             getattr(lib, fn).restype = ci
         _lib = lib
         return lib
@@ -178,6 +181,53 @@ def decode_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = 
                                   stop, freeze, 1 if fp32 else 0, nthreads, _p(u_hat, ctypes.c_uint8),
                                   _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double))
     _check(rc, "decode_batch")
+    return u_hat, iters, pe, margin
+
+
+def decode_flood(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE, fp32: bool = False,
+                 trace: bool = False) -> dict:
+    """Decode one codeword under the true flooding schedule (every PE of every stage
+    from iteration t-1's messages; no freezing).  Returns u_hat, iters, pe, margin and,
+    with ``trace``, the L / R planes after each iteration ([iters, m+1, N])."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    N = frozen.shape[0]
+    m = N.bit_length() - 1
+    u_hat = np.zeros(N, np.uint8)
+    iters = np.zeros(1, np.int32)
+    pe = np.zeros(1, np.int64)
+    margin = np.zeros(1, np.float64)
+    tl = tr = None
+    if trace:
+        tl = np.full((max_iter, m + 1, N), np.nan, np.float64)
+        tr = np.full((max_iter, m + 1, N), np.nan, np.float64)
+    rc = _load().orc_decode_flood(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), max_iter, alpha, stop,
+                                  1 if fp32 else 0, _p(u_hat, ctypes.c_uint8), _p(iters, ctypes.c_int32),
+                                  _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double), _p(tl, ctypes.c_double),
+                                  _p(tr, ctypes.c_double))
+    _check(rc, "decode_flood")
+    out = {"u_hat": u_hat, "iters": int(iters[0]), "pe": int(pe[0]), "margin": float(margin[0])}
+    if trace:
+        n = out["iters"]
+        out.update(L=tl[:n], R=tr[:n])
+    return out
+
+
+def decode_flood_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE,
+                       fp32: bool = False, nthreads: int = 0):
+    """Flooding-schedule decode of a [batch, N] LLR array; returns (u_hat, iters, pe, margin)."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    B, N = llr.shape
+    u_hat = np.zeros((B, N), np.uint8)
+    iters = np.zeros(B, np.int32)
+    pe = np.zeros(B, np.int64)
+    margin = np.zeros(B, np.float64)
+    rc = _load().orc_decode_flood_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B, max_iter,
+                                        alpha, stop, 1 if fp32 else 0, nthreads, _p(u_hat, ctypes.c_uint8),
+                                        _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64),
+                                        _p(margin, ctypes.c_double))
+    _check(rc, "decode_flood_batch")
     return u_hat, iters, pe, margin
 
 

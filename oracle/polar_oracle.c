@@ -475,6 +475,128 @@ out:
     return rc;
 }
 
+/*
+ * True flooding schedule, a variant beside the sweep of Eq. (1).  The paper
+ * activates the PEs stage by stage from left to right (Sec. II-A), so R comes
+ * from the current iteration and L from the previous one.  Under flooding,
+ * every PE of every stage takes both its L and its R inputs from iteration
+ * t-1, and all PEs update together.  Column 0's R (the channel) and column m's
+ * L (the prior) are constant.  Messages start as in R2: interior L and R at 0.
+ * The PE is Eq. (1)'s, with the same operand order.  There is no CSFG freezing:
+ * its order of checks is defined on the sweep.  Stop modes, the output and the
+ * PE count (m N/2 per iteration) are those of the sweep without freezing.
+ */
+int orc_decode_flood(int N, const uint8_t* frozen, const float* llr, int max_iter, double alpha, int stop_mode,
+                     int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin, double* trace_L,
+                     double* trace_R)
+{
+    int m = ilog2_exact(N);
+    if (m < 1 || !frozen || !llr || max_iter < 1 || !(alpha > 0.0) || !u_hat) return ORC_ERR_ARG;
+    dec_t d;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.m = m;
+    d.fp32 = fp32;
+    d.alpha = fp32 ? (double)(float)alpha : alpha;
+    d.frozen = frozen;
+    d.margin = INFINITY;
+    size_t planes = (size_t)(m + 1) * (size_t)N;
+    d.L = (double*)calloc(planes, sizeof(double));
+    d.R = (double*)calloc(planes, sizeof(double));
+    double* Ln = (double*)calloc(planes, sizeof(double));
+    double* Rn = (double*)calloc(planes, sizeof(double));
+    d.uh = (uint8_t*)malloc((size_t)N);
+    d.scratch = (uint8_t*)malloc((size_t)N);
+    d.ubits = (uint8_t*)malloc((size_t)N);
+    int rc = ORC_OK;
+    if (!d.L || !d.R || !Ln || !Rn || !d.uh || !d.scratch || !d.ubits) {
+        rc = ORC_ERR_NOMEM;
+        goto out;
+    }
+    for (int i = 0; i < N; ++i) {
+        LM(&d, m, i) = frozen[i] ? INFINITY : 0.0; /* reading R2 */
+        RM(&d, 0, i) = (double)llr[i];
+    }
+    int done = 0, t_done = max_iter;
+    for (int t = 1; t <= max_iter && !done; ++t) {
+        memcpy(Ln, d.L, planes * sizeof(double)); /* keeps L[m], the prior */
+        memcpy(Rn, d.R, planes * sizeof(double)); /* keeps R[0], the channel */
+        for (int s = 0; s < m; ++s) {
+            const int h = 1 << (m - 1 - s);
+            for (int a = 0; a < N; ++a) {
+                if (a & h) continue;
+                const int b = a + h;
+                const double La = LM(&d, s + 1, a); /* L^{t-1}_{i,j+1}        */
+                const double Lb = LM(&d, s + 1, b); /* L^{t-1}_{i+2^(m-j),j+1} */
+                const double Ra = RM(&d, s, a);     /* R^{t-1}_{i,j}          */
+                const double Rb = RM(&d, s, b);     /* R^{t-1}_{i+2^(m-j),j}  */
+                const double tt = rnd(&d, Lb + Rb);
+                const double g = fms(&d, La, Ra);
+                const double nLa = fms(&d, La, tt);
+                const double nLb = rnd(&d, Lb + g);
+                const double nRa = fms(&d, Ra, tt);
+                const double nRb = rnd(&d, Rb + g);
+                if (isnan(nLa) || isnan(nLb) || isnan(nRa) || isnan(nRb)) d.nan_seen = 1;
+                Ln[(size_t)s * N + a] = nLa;
+                Ln[(size_t)s * N + b] = nLb;
+                Rn[(size_t)(s + 1) * N + a] = nRa;
+                Rn[(size_t)(s + 1) * N + b] = nRb;
+                d.pe += 1;
+            }
+        }
+        memcpy(d.L, Ln, planes * sizeof(double));
+        memcpy(d.R, Rn, planes * sizeof(double));
+        if (d.nan_seen) {
+            rc = ORC_ERR_NAN;
+            goto out;
+        }
+        if (stop_mode == 1 && gmatrix_stop(&d, 0)) done = 1;
+        if (trace_L) memcpy(trace_L + (size_t)(t - 1) * planes, d.L, planes * sizeof(double));
+        if (trace_R) memcpy(trace_R + (size_t)(t - 1) * planes, d.R, planes * sizeof(double));
+        if (done) t_done = t;
+    }
+    for (int i = 0; i < N; ++i) u_hat[i] = source_bit(&d, i, 0);
+    if (iters) *iters = t_done;
+    if (pe) *pe = d.pe;
+    if (margin) *margin = d.margin;
+out:
+    free(d.L);
+    free(d.R);
+    free(Ln);
+    free(Rn);
+    free(d.uh);
+    free(d.scratch);
+    free(d.ubits);
+    return rc;
+}
+
+int orc_decode_flood_batch(int N, const uint8_t* frozen, const float* llr, int batch, int max_iter, double alpha,
+                           int stop_mode, int fp32, int nthreads, uint8_t* u_hat, int32_t* iters, int64_t* pe,
+                           double* margin)
+{
+    if (batch < 0) return ORC_ERR_ARG;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+#endif
+    for (int c = 0; c < batch; ++c) {
+        int r = orc_decode_flood(N, frozen, llr + (size_t)c * (size_t)N, max_iter, alpha, stop_mode, fp32,
+                                 u_hat + (size_t)c * (size_t)N, iters ? iters + c : NULL, pe ? pe + c : NULL,
+                                 margin ? margin + c : NULL, NULL, NULL);
+        if (r != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            {
+                if (err == ORC_OK) err = r;
+            }
+        }
+    }
+    (void)nthreads;
+    return err;
+}
+
 /* Decode `batch` codewords (llr is batch x N), threaded over codewords when the
  * file is built with OpenMP.  nthreads <= 0 uses the OpenMP default.  Returns
  * the first nonzero error code met, else ORC_OK. */

@@ -359,3 +359,81 @@ def test_n8_freeze_hand_trace():
                     for i, v in vals.items():
                         want = np.inf if v == "inf" else float(v)
                         assert o[plane][t][int(c), int(i)] == want, (stop, t, plane, c, i)
+
+
+# --------------------------------------------------------------------------
+# True flooding schedule (a variant beside the sweep of Eq. (1)): every PE takes
+# both its L and its R inputs from the previous iteration
+# --------------------------------------------------------------------------
+def test_flooding_n4_hand_trace():
+    g = json.load(open(os.path.join(GOLDEN, "n4_flooding.json")))
+    conv = lambda v: [np.inf if e == "inf" else (-np.inf if e == "-inf" else e) for e in v]
+    r = O.decode_flood(np.array(g["frozen"], np.uint8), np.array(g["llr"], np.float32), 2, alpha=g["alpha"],
+                       trace=True)
+    for it, key in ((0, "iter1"), (1, "iter2")):
+        e = g[key]
+        assert r["R"][it][1].tolist() == conv(e["R1"])
+        assert r["R"][it][2].tolist() == conv(e["R2"])
+        assert r["L"][it][0].tolist() == conv(e["L0"])
+        assert r["L"][it][1].tolist() == conv(e["L1"])
+    assert r["u_hat"].tolist() == g["u_hat"] and r["pe"] == g["pe"]
+
+
+def test_flooding_n2_equals_sweep():
+    """With one stage there is no interior column: both schedules read only the channel
+    and the prior, so every message of every iteration is the sweep's (itself pinned by
+    the N = 2 closed forms)."""
+    rng = np.random.default_rng(9)
+    for fz in ([1, 0], [0, 0], [1, 1]):
+        fz = np.array(fz, np.uint8)
+        for _ in range(50):
+            llr = rng.normal(0, 3, 2).astype(np.float32)
+            a = O.decode(fz, llr, 4, trace=True)
+            b = O.decode_flood(fz, llr, 4, trace=True)
+            assert np.array_equal(a["L"], b["L"]) and np.array_equal(a["R"], b["R"])
+            assert np.array_equal(a["u_hat"], b["u_hat"]) and a["pe"] == b["pe"]
+
+
+@pytest.mark.parametrize("N", [8, 64, 256])
+def test_flooding_moves_one_column_per_iteration(N):
+    """Interior messages start at 0 and a PE whose L (R) inputs are all 0 emits 0 on
+    that side, so after t < m iterations R[s] = 0 for s > t and L[s] = 0 for s < m - t;
+    the sweep, by contrast, reaches R[m] in its first iteration."""
+    m = N.bit_length() - 1
+    fz, u, x, llr = _noisy(N, N // 2, 3, 2.0, 21)
+    for c in range(llr.shape[0]):
+        r = O.decode_flood(fz, llr[c], m, trace=True)
+        for t in range(1, m):
+            R, L = r["R"][t - 1], r["L"][t - 1]
+            assert np.all(R[t + 1:] == 0) and np.any(R[t] != 0)
+            assert np.all(L[:m - t] == 0)
+        assert np.any(O.decode(fz, llr[c], 1, trace=True)["R"][0][m] != 0)
+
+
+@pytest.mark.parametrize("N", [8, 64, 1024])
+def test_flooding_noiseless_stops_at_iteration_m(N):
+    """Noiseless input: every message sign agrees with the codeword, and R[m] stays 0 until
+    the channel's wavefront reaches it in iteration m.  So for a nonzero source word the
+    G-matrix test fails before iteration m and passes exactly there, with u_hat = u;
+    fixed iterations t < m decide 0 on every information position."""
+    m = N.bit_length() - 1
+    fz = O.bec_frozen(N, N // 2)
+    u = I.info_bits(12, np.arange(4), fz)
+    x = O.encode(u)
+    llr = I.noiseless_llr(x, 2.5)
+    for c in range(4):
+        assert u[c].any()
+        r = O.decode_flood(fz, llr[c], 3 * m, stop=O.STOP_GMATRIX)
+        assert (r["iters"], r["pe"]) == (m, m * m * N // 2) and np.array_equal(r["u_hat"], u[c])
+        r = O.decode_flood(fz, llr[c], m - 1)
+        assert not r["u_hat"].any()
+        r = O.decode_flood(fz, llr[c], m)
+        assert np.array_equal(r["u_hat"], u[c])
+
+
+def test_flooding_batch_matches_single_and_fp32():
+    fz, u, x, llr = _noisy(64, 32, 30, 2.5, 33)
+    uh, it, pe, _ = O.decode_flood_batch(fz, llr, 40, stop=O.STOP_GMATRIX, fp32=True)
+    for c in range(llr.shape[0]):
+        r = O.decode_flood(fz, llr[c], 40, stop=O.STOP_GMATRIX, fp32=True)
+        assert np.array_equal(uh[c], r["u_hat"]) and it[c] == r["iters"] and pe[c] == r["pe"]
