@@ -151,6 +151,31 @@ int polarbp_decode_trace(const polarbp_code* code, const float* llr, int batch, 
                          int64_t* pe_updates, float* trace_L, float* trace_R, int32_t* trace_P, void* stream);
 
 /*
+ * polarbp_decode_flooding -- BP decoding under the true flooding schedule, a
+ * variant beside the left-to-right sweep of Eq. (1) (Sec. II-A): in every
+ * iteration every PE of every stage takes both its L and its R inputs from
+ * the previous iteration, and all PEs update together.  The PE update, the
+ * scaling, the prior (+inf on frozen positions, 0 elsewhere), the zero start
+ * of interior messages, the G-matrix stop and the output are those of
+ * polarbp_decode without freezing; CSFG freezing (Sec. III) is defined on the
+ * sweep and is not offered here.
+ *   llr, batch, max_iter, scale, u_hat, iterations, pe_updates
+ *                    as polarbp_decode (device buffers; iterations and
+ *                    pe_updates may be NULL; pe_updates = iterations m N/2).
+ *   stop_mode        POLARBP_STOP_NONE or POLARBP_STOP_GMATRIX.
+ *   trace_L, trace_R NULL, or both [batch][max_iter][m+1][N] binary32 device
+ *                    buffers receiving the planes after every iteration
+ *                    (iterations after the stop are left untouched).
+ * N <= 1024 (the planes of one codeword, 8 (m+1) N bytes, sit in shared
+ * memory); larger codes return POLARBP_ERR_UNSUPPORTED.  Non-finite LLRs are
+ * recorded in the status word.  Errors: POLARBP_ERR_ARG,
+ * POLARBP_ERR_UNSUPPORTED, POLARBP_ERR_CUDA.
+ */
+int polarbp_decode_flooding(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
+                            int stop_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates,
+                            float* trace_L, float* trace_R, void* stream);
+
+/*
  * polarbp_decode_host_workspace -- bytes of device workspace polarbp_decode_host
  * needs for `batch` codewords (256-byte aligned sub-buffers).
  */

@@ -362,6 +362,7 @@ int noalloc_scratch_address(void** out)
 // accessors shared with the other translation units of the library
 namespace polarbp_internal {
 const uint32_t* frozen_words(const polarbp_code* c) { return c->d_frozen; }
+unsigned int* status_word(const polarbp_code* c) { return c->d_status; }
 int fail(int code, const std::string& msg) { return ::fail(code, msg); }
 int cuda_fail(cudaError_t e, const char* what) { return ::cuda_fail(e, what); }
 int check_device(const polarbp_code* c) { return ::check_device(c); }
