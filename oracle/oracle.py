@@ -27,6 +27,7 @@ STOP_NONE = 0
 STOP_GMATRIX = 1
 FREEZE_OFF = 0
 FREEZE_CSFG = 1
+FREEZE_CSFG_MULTI = 2  # reading B: checks continue along a level while they pass (a variant)
 
 
 def build(force: bool = False) -> str:

@@ -32,7 +32,9 @@
  *       positions, 0 on information positions.
  *   R3  level j is checked right after PE stage j-1 (it consumes R[j]), and
  *       only its first CSFG that is not yet covered is checked, once per
- *       iteration (Sec. III; Fig. 5 captions).
+ *       iteration (Sec. III; Fig. 5 captions).  Reading B, offered as a
+ *       variant (freeze = 2), keeps checking along the level, on the same
+ *       R[j], while the checks pass.
  *   R4  a CSFG is "covered" when it, or a CSFG containing it, is frozen.  A
  *       CSFG whose two halves are both covered is frozen at that moment, with
  *       the hard decision obtained by re-encoding the stored source bits of
@@ -308,19 +310,25 @@ static void freeze_block(dec_t* d, int j, int k, const uint8_t* xh, const uint8_
     }
 }
 
-/* Check the first uncovered CSFG of level j (reading R3). */
-static void check_level(dec_t* d, int j)
+/* Check the first uncovered CSFG of level j (reading R3).  With multi set
+ * (reading B, a variant) a CSFG that passes is frozen and the next one of the
+ * same level is checked at once, on the same R[j], until one fails or the
+ * level is covered. */
+static void check_level(dec_t* d, int j, int multi)
 {
     int S = d->N >> j;
     int nblk = 1 << j;
-    int k = 0;
-    while (k < nblk && covered(d, j, k)) ++k;
-    if (k == nblk) return;
-    int base = k * S;
-    const double* Rin = &RM(d, j, base);
-    for (int i = 0; i < S; ++i) note_margin(d, Rin[i]);
-    if (orc_csfg_check(S, Rin, d->frozen + base, d->xh, d->uh, d->scratch))
+    for (;;) {
+        int k = 0;
+        while (k < nblk && covered(d, j, k)) ++k;
+        if (k == nblk) return;
+        int base = k * S;
+        const double* Rin = &RM(d, j, base);
+        for (int i = 0; i < S; ++i) note_margin(d, Rin[i]);
+        if (!orc_csfg_check(S, Rin, d->frozen + base, d->xh, d->uh, d->scratch)) return;
         freeze_block(d, j, k, d->xh, d->uh);
+        if (!multi) return;
+    }
 }
 
 /* PE stage s (Eq. (1)), skipping PEs inside covered CSFGs (reading R5). */
@@ -381,7 +389,9 @@ static int gmatrix_stop(dec_t* d, int use_store)
  * Decode one codeword.
  *   llr        N channel LLRs, log P(x=0)/P(x=1), as binary32
  *   stop_mode  0 = fixed iterations, 1 = G-matrix stop
- *   freeze     0 = off, 1 = CSFG freezing
+ *   freeze     0 = off, 1 = CSFG freezing (reading R3: one check per level per
+ *              iteration), 2 = CSFG freezing under reading B (a variant: at
+ *              each level, checks continue along the level while they pass)
  *   u_hat      N output bytes (0/1)
  *   iters      iterations executed; pe = PE updates executed (Sec. IV count)
  *   margin     smallest |value| a hard decision was taken on (may be NULL)
@@ -428,7 +438,7 @@ int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, dou
         for (int i = 0; i < N; ++i) RM(&d, 0, i) = (double)llr[i];
         for (int s = 0; s < m; ++s) {
             if (freeze && s >= 1) {
-                check_level(&d, s);
+                check_level(&d, s, freeze == 2);
                 if (covered_prefix(&d) == N) {
                     done = 1;
                     break;
@@ -437,7 +447,7 @@ int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, dou
             pe_stage(&d, s);
         }
         if (!done && freeze) {
-            check_level(&d, m);
+            check_level(&d, m, freeze == 2);
             if (covered_prefix(&d) == N) done = 1;
         }
         if (!done && stop_mode == 1) {

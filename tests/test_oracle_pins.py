@@ -437,3 +437,58 @@ def test_flooding_batch_matches_single_and_fp32():
     for c in range(llr.shape[0]):
         r = O.decode_flood(fz, llr[c], 40, stop=O.STOP_GMATRIX, fp32=True)
         assert np.array_equal(uh[c], r["u_hat"]) and it[c] == r["iters"] and pe[c] == r["pe"]
+
+
+# --------------------------------------------------------------------------
+# Reading B of the freezing order (a variant): after a CSFG of stage j passes,
+# the next CSFG of stage j is checked at once, on the same R[j]
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [8, 64, 1024])
+@pytest.mark.parametrize("frac", [0.25, 0.5, 0.75])
+def test_reading_b_noiseless_freezes_stage_1(N, frac):
+    """Noiseless input, iteration 1: after stage 0, R[1] = (f(y_a, y_b), y_b) with L[1] = 0, whose
+    hard decisions are the encodings of the two halves of u.  Both stage-1 CSFGs pass, so reading B
+    covers everything after N/2 PE updates, with or without the G-matrix stop (reading A needs
+    2 iterations and 3N/2 - 1 PEs there)."""
+    K = int(N * frac)
+    fz = O.bec_frozen(N, K)
+    u = I.info_bits(11, np.arange(4), fz)
+    llr = I.noiseless_llr(O.encode(u), 2.5)
+    for c in range(4):
+        for stop in (O.STOP_NONE, O.STOP_GMATRIX):
+            r = O.decode(fz, llr[c], 30, stop=stop, freeze=O.FREEZE_CSFG_MULTI)
+            assert (r["iters"], r["pe"]) == (1, N // 2) and np.array_equal(r["u_hat"], u[c])
+
+
+def test_reading_b_n8_hand_trace_extra_check_fails():
+    """The hand-traced (8,4) example: in iteration 1 the stage-1 CSFG [0,4) freezes, and reading B
+    then checks [4,8) on the same R1 = (4, 6, -1, 2): x = (0,0,1,0), u = x F = (1,0,1,0), and u(4) = 1
+    sits on a frozen position, so it fails; deeper stages and iteration 2 go as under reading A.
+    Every value of the fixture must therefore come out unchanged."""
+    g = json.load(open(os.path.join(GOLDEN, "n8_freeze_hand_trace.json")))
+    conv = lambda v: np.inf if v == "inf" else (-np.inf if v == "-inf" else v)
+    r = O.decode(np.array(g["frozen"], np.uint8), np.array(g["llr"], np.float32), g["max_iter"], alpha=g["alpha"],
+                 freeze=O.FREEZE_CSFG_MULTI, trace=True)
+    for t, e in enumerate(g["iterations"]):
+        assert int(r["P"][t]) == e["P"] and int(r["pe_iter"][t]) == e["pe"]
+        for col, vals in e["R"].items():
+            for i, v in vals.items():
+                assert r["R"][t][int(col)][int(i)] == conv(v)
+        for col, vals in e["L"].items():
+            for i, v in vals.items():
+                assert r["L"][t][int(col)][int(i)] == conv(v)
+    assert r["u_hat"].tolist() == g["u_hat"]
+
+
+@pytest.mark.parametrize("N", [16, 64, 256])
+def test_reading_b_covers_at_least_reading_a_in_iteration_1(N):
+    """In iteration 1 a checked CSFG's R comes from PEs of enclosing CSFGs that are uncovered under
+    both readings, all fed by the channel and the zero start, so both readings see the same values
+    on it.  Stage by stage, reading B's prefix is then at least reading A's: on the same candidate it
+    takes the same decision and may go on along the stage; on a later candidate, A's candidate ends
+    before B's prefix."""
+    fz, u, x, llr = _noisy(N, N // 2, 40, 3.0, 41)
+    for c in range(llr.shape[0]):
+        a = O.decode(fz, llr[c], 1, freeze=O.FREEZE_CSFG, trace=True)
+        b = O.decode(fz, llr[c], 1, freeze=O.FREEZE_CSFG_MULTI, trace=True)
+        assert int(b["P"][0]) >= int(a["P"][0])
