@@ -631,6 +631,56 @@ def run_flooding(args):
     return 0
 
 
+def run_readings(args):
+    """The freezing order of Sec. III under reading A (one check per stage per iteration, the
+    build's reading) and reading B (checks continue along a stage while they pass), with the
+    G-matrix stop, on the same (1024,512) codewords at 2.5, 3.0 and 3.5 dB, max 60 iterations:
+    FER with Wilson 95 % intervals, iterations, PE updates per codeword and info Gbit/s."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n_cw = 1 << 20
+    code = B.polarbp_construct(N, K)
+    uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
+    it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
+    pe = torch.empty(n_cw, dtype=torch.int64, device="cuda")
+    points = []
+    with ClockSampler(0) as clk:
+        for eb in (2.5, 3.0, 3.5):
+            u, llr = B.polarbp_awgn(code, SEED + 13, 0, n_cw, eb)
+            row = {"ebn0_db": eb, "codewords": n_cw}
+            for name, fm in (("reading_A", 1), ("reading_B", 2)):
+                B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, fm, uh, it, pe, stream=stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, fm, uh, it, pe, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                errs = int((uh != u).any(dim=1).sum().item())
+                pe_sum = float(pe.double().sum().item())
+                row[name] = {"fer": errs / n_cw, "fer_ci95": list(wilson(errs, n_cw)),
+                             "avg_iters": float(it.double().mean().item()), "pe_per_codeword": pe_sum / n_cw,
+                             "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9, "ms": ms,
+                             "alu_frac": pe_sum / (ms * 1e-3) / PEAK_PE_PER_S}
+            points.append(row)
+            del u, llr
+            torch.cuda.empty_cache()
+    head = next(p for p in points if p["ebn0_db"] == 3.0)["reading_B"]
+    line = {"metric": "freezing order readings A and B, (1024,512), G-matrix stop, FER / PE updates / Gbit/s",
+            "unit": "Gbit/s", "value": head["info_gbit_s"], "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"(1024,512) code, {n_cw} codewords per point, alpha {ALPHA}, max 60 "
+                                   "iterations, device generator"},
+            "points": points, "clocks": clk.summary(), "gpu_launches": 2 * 2 * len(points)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_long(args):
     """Long codes: N in {8192, 16384, 32768}, K = N/2, Eb/N0 in {2.0, 2.5, 3.0} dB, 10^5
     codewords per point (device generator), G-matrix stop + CSFG freezing, at most 100
@@ -834,10 +884,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--sweep-codewords", type=int, default=1000000)
-    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms", "sweep", "flooding"], default="n1024",
+    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms", "sweep", "flooding", "readings"],
+                    default="n1024",
                     help="n1024: the (1024,512) headline; mixed: the mixed-length stream; long: N = 8192..32768 "
                          "on thread-block clusters; wms: learned weights; sweep: FER over Eb/N0; flooding: the "
-                         "true flooding schedule against the sweep")
+                         "true flooding schedule against the sweep; readings: freezing order A against B")
     ap.add_argument("--long-codewords", type=int, default=100000)
     ap.add_argument("--long-n", type=int, default=0, help="one code length of the long workload (default: all)")
     ap.add_argument("--long-ebn0", type=float, default=None, help="one Eb/N0 point of the long workload")
@@ -855,6 +906,8 @@ def main():
         return run_long(args)
     if args.workload == "flooding":
         return run_flooding(args)
+    if args.workload == "readings":
+        return run_readings(args)
     if args.workload == "sweep":
         return run_sweep(args)
     return run_ours(args)

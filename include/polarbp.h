@@ -45,8 +45,9 @@ typedef enum polarbp_stop_mode {
 } polarbp_stop_mode;
 
 typedef enum polarbp_freeze_mode {
-    POLARBP_FREEZE_OFF = 0,  /* every PE of every stage runs every iteration */
-    POLARBP_FREEZE_CSFG = 1  /* connected-sub-factor-graph freezing, Sec. III */
+    POLARBP_FREEZE_OFF = 0,        /* every PE of every stage runs every iteration */
+    POLARBP_FREEZE_CSFG = 1,       /* connected-sub-factor-graph freezing, Sec. III */
+    POLARBP_FREEZE_CSFG_MULTI = 2  /* a variant reading of Sec. III: checks continue along a stage */
 } polarbp_freeze_mode;
 
 /* Opaque code handle: the frozen set plus its device-side tables.  Owned by the
@@ -118,6 +119,12 @@ int polarbp_encode(const polarbp_code* code, const uint8_t* u, uint8_t* x, int b
  *                PEs are skipped from then on.  A CSFG whose two halves are
  *                covered is frozen too.  Decoding ends once every position is
  *                covered, at the G-matrix stop, or at max_iter.
+ *                POLARBP_FREEZE_CSFG_MULTI reads Sec. III's "move to the next
+ *                stage" as coming only after a failing check: a CSFG that passes
+ *                is frozen and the next CSFG of the same stage is checked at
+ *                once, on the same R, until one fails.  It is a variant for
+ *                comparison (it raises FER sharply, see the design notes);
+ *                N <= 4096, polarbp_decode and polarbp_decode_trace only.
  *   u_hat        device [batch][N] decoded source bits (0 on frozen positions).
  *   iterations   device [batch] int32 iterations run, or NULL.
  *   pe_updates   device [batch] int64 PE updates executed, counted as in

@@ -27,6 +27,7 @@ POLARBP_STOP_NONE = 0
 POLARBP_STOP_GMATRIX = 1
 POLARBP_FREEZE_OFF = 0
 POLARBP_FREEZE_CSFG = 1
+POLARBP_FREEZE_CSFG_MULTI = 2
 
 _lock = threading.Lock()
 _lib = None

@@ -143,6 +143,7 @@ struct DecodeArgs {
     int batch;
     int max_iter;
     float alpha;
+    int multi;  // reading B: checks continue along a stage while they pass (a variant)
 };
 
 // Pointers of one codeword (trace pointers already offset to the codeword).
@@ -392,11 +393,14 @@ __device__ __forceinline__ void polar_xform(uint32_t (&v)[RW], int S, int lane)
 // ---------------------------------------------------------------------------
 // checker warp
 // ---------------------------------------------------------------------------
+// Record the feedback event [lo, hi) on column J.  Under reading B a column can
+// take several events in one iteration; they are consecutive CSFGs (P only
+// grows, and by steps no larger than the column's CSFGs), so the range grows.
 template <int M>
 __device__ __forceinline__ void note_event(Smem<M>& sm, int J, int lo, int hi, int lane)
 {
     if (lane == 0) {
-        sm.ev_lo()[J] = lo;
+        if (!(sm.ctl[CTL_EVENT] & (1 << J))) sm.ev_lo()[J] = lo;
         sm.ev_hi()[J] = hi;
         sm.ctl[CTL_EVENT] |= 1 << J;
     }
@@ -570,7 +574,7 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, const SpecSl
 // the PE updates of the iteration (Sec. IV count; stage s runs the PEs outside
 // covered CSFGs given P after the check of stage s).
 template <int M>
-__device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
+__device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane, bool multi)
 {
     using SP = Spec<M>;
     constexpr int N = Geo<M>::N, NW = Geo<M>::NW;
@@ -610,7 +614,7 @@ __device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
         __syncwarp();
         propagate<M>(sm, P, J, lane);
         if (lane >= J) Ps = P;
-        jmin = J + 1;
+        jmin = multi ? J : J + 1;  // reading B checks the next CSFG of the same stage, on the same R[J]
     }
     const int pe = (lane >= 1 && lane < M) ? (N - ((Ps >> (M - lane)) << (M - lane))) >> 1 : 0;
     return (int)__reduce_add_sync(kFull, (unsigned)pe) + (N >> 1);
@@ -724,7 +728,7 @@ __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
 }
 
 template <int M, bool GSTOP, bool FREEZE>
-__device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
+__device__ __forceinline__ void checker(unsigned char* smem_base, int lane, bool multi)
 {
     constexpr int N = Geo<M>::N;
     Smem<M> sm(smem_base);
@@ -737,7 +741,7 @@ __device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
     int P = sm.ctl[CTL_P];
     int pe_it = N >> 1;  // stage 0 always runs
     if constexpr (FREEZE) {
-        pe_it = resolve<M>(sm, P, lane);
+        pe_it = resolve<M>(sm, P, lane, multi);
     } else {
         pe_it = M * (N >> 1);
     }
@@ -1115,7 +1119,7 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
 // the group) on the group's shared memory smem_raw.
 template <int M, bool GSTOP, bool FREEZE, bool TRACE, int CPC>
 __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, float alpha, unsigned int* status,
-                                                unsigned char* smem_raw, int tid, int grp)
+                                                unsigned char* smem_raw, int tid, int grp, bool multi = false)
 {
     using G = Geo<M>;
     constexpr int N = G::N, EL = G::EL, T = G::T, NW = G::NW;
@@ -1174,7 +1178,7 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
         group_sync<G::BLOCK, CPC>(grp);
         bool done = false;
         if constexpr (GSTOP || FREEZE) {
-            if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane);
+            if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane, multi);
             group_sync<G::BLOCK, CPC>(grp);
             done = sm.ctl[CTL_DONE] != 0;
             if constexpr (FREEZE) {
@@ -1233,7 +1237,8 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::min_blocks(FREEZE)) bp_
                   TRACE ? a.trace_L + tb : nullptr,
                   TRACE ? a.trace_R + tb : nullptr,
                   TRACE ? a.trace_P + cw * a.max_iter : nullptr};
-    decode_codeword<M, GSTOP, FREEZE, TRACE, 1>(io, a.max_iter, a.alpha, a.status, smem_raw, threadIdx.x, 0);
+    decode_codeword<M, GSTOP, FREEZE, TRACE, 1>(io, a.max_iter, a.alpha, a.status, smem_raw, threadIdx.x, 0,
+                                                a.multi != 0);
 }
 
 // Persistent decoding of a queue of codewords split in segments (one code per

@@ -234,8 +234,11 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     if (!(scale > 0.f) || !std::isfinite(scale)) return fail(POLARBP_ERR_ARG, "scale must be finite and > 0");
     if (stop_mode != POLARBP_STOP_NONE && stop_mode != POLARBP_STOP_GMATRIX)
         return fail(POLARBP_ERR_ARG, "unknown stop_mode");
-    if (freeze_mode != POLARBP_FREEZE_OFF && freeze_mode != POLARBP_FREEZE_CSFG)
+    if (freeze_mode != POLARBP_FREEZE_OFF && freeze_mode != POLARBP_FREEZE_CSFG &&
+        freeze_mode != POLARBP_FREEZE_CSFG_MULTI)
         return fail(POLARBP_ERR_ARG, "unknown freeze_mode");
+    if (freeze_mode == POLARBP_FREEZE_CSFG_MULTI && c->m > 12)
+        return fail(POLARBP_ERR_UNSUPPORTED, "POLARBP_FREEZE_CSFG_MULTI supports N <= 4096");
     if (batch == 0) return POLARBP_OK;
     if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be device pointers");
     if (trace && (!trace_L || !trace_R || !trace_P)) return fail(POLARBP_ERR_ARG, "trace buffers must be given");
@@ -256,6 +259,7 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     q.args.batch = batch;
     q.args.max_iter = max_iter;
     q.args.alpha = scale;
+    q.args.multi = freeze_mode == POLARBP_FREEZE_CSFG_MULTI ? 1 : 0;
     q.stop_mode = stop_mode;
     q.freeze_mode = freeze_mode;
     q.trace = trace;

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 MODES = [(0, 0), (1, 0), (0, 1), (1, 1)]  # (stop_mode, freeze_mode)
+MODES_B = [(0, 2), (1, 2)]  # freezing under reading B (checks continue along a stage while they pass)
 ALPHA = 0.9375
 
 
@@ -85,7 +86,7 @@ def test_device_generator_matches_host_generator(B, N, K):
 
 
 @pytest.mark.parametrize("N", [2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
-@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mode", MODES + MODES_B)
 def test_decode_matches_binary32_oracle(B, N, mode):
     K = N // 2
     batch = 96 if N <= 1024 else 24
@@ -101,7 +102,7 @@ def test_decode_matches_binary32_oracle(B, N, mode):
 
 
 @pytest.mark.parametrize("N", [8, 16, 64, 128, 512, 1024, 4096])
-@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mode", MODES + MODES_B)
 def test_message_planes_match_binary32_oracle(B, N, mode):
     K = N // 2
     M = N.bit_length() - 1
@@ -368,3 +369,16 @@ def test_n8_freeze_hand_trace(B):
                     for i, v in vals.items():
                         want = np.inf if v == "inf" else float(v)
                         assert arr[0, t, int(c), int(i)] == want, (stop, t, plane, c, i)
+
+
+def test_reading_b_limits(B):
+    """Reading B runs on the one-block kernels only (N <= 4096)."""
+    code = B.polarbp_construct(8192, 4096)
+    llr = torch.zeros((1, 8192), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.PolarBPError) as e:
+        B.polarbp_decode(code, llr, 5, ALPHA, 1, B.POLARBP_FREEZE_CSFG_MULTI)
+    assert e.value.code == B.POLARBP_ERR_UNSUPPORTED
+    with pytest.raises(B.PolarBPError) as e:
+        B.polarbp_decode(B.polarbp_construct(64, 32), torch.zeros((1, 64), dtype=torch.float32, device="cuda"),
+                         5, ALPHA, 1, 3)
+    assert e.value.code == B.POLARBP_ERR_ARG
