@@ -58,17 +58,20 @@ def _load():
         lib.orc_bec_frozen.argtypes = [ci, ci, cd, u8p]
         lib.orc_encode.argtypes = [ci, u8p, u8p]
         lib.orc_csfg_check_ext.argtypes = [ci, f64p, u8p, u8p, u8p]
-        lib.orc_decode.argtypes = [ci, u8p, f32p, ci, cd, ci, ci, ci, u8p, i32p, i64p, f64p,
+        lib.orc_decode.argtypes = [ci, u8p, f32p, ci, cd, ci, ci, ci, u8p, i32p, i64p, f64p, i32p,
                                    f64p, f64p, i32p, i64p]
         lib.orc_decode_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, ci, u8p, i32p, i64p,
-                                         f64p]
+                                         f64p, i32p]
         lib.orc_decode_flood.argtypes = [ci, u8p, f32p, ci, cd, ci, ci, u8p, i32p, i64p, f64p, f64p, f64p]
         lib.orc_decode_flood_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, u8p, i32p, i64p, f64p]
+        lib.orc_sc_decode.argtypes = [ci, u8p, f32p, ci, u8p]
+        lib.orc_sc_decode_batch.argtypes = [ci, u8p, f32p, ci, ci, ci, u8p]
         lib.orc_max_threads.argtypes = []
         lib.orc_wms_forward.argtypes = [ci, u8p, f32p, ci, f64p, ci, f64p, f64p, f64p]
         lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, f64p, f64p]
         for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
-                   "orc_decode_batch", "orc_decode_flood", "orc_decode_flood_batch", "orc_max_threads",
+                   "orc_decode_batch", "orc_decode_flood", "orc_decode_flood_batch", "orc_sc_decode",
+                   "orc_sc_decode_batch", "orc_max_threads",
                    "orc_wms_forward", "orc_wms_backward"):
             getattr(lib, fn).restype = ci
         _lib = lib
@@ -150,6 +153,7 @@ def decode(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_N
     iters = np.zeros(1, np.int32)
     pe = np.zeros(1, np.int64)
     margin = np.zeros(1, np.float64)
+    cover = np.zeros(1, np.int32)
     tl = tr = tp = tpe = None
     if trace:
         tl = np.full((max_iter, m + 1, N), np.nan, np.float64)
@@ -158,10 +162,12 @@ def decode(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_N
         tpe = np.zeros(max_iter, np.int64)
     rc = _load().orc_decode(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), max_iter, alpha, stop,
                             freeze, 1 if fp32 else 0, _p(u_hat, ctypes.c_uint8), _p(iters, ctypes.c_int32),
-                            _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double), _p(tl, ctypes.c_double),
-                            _p(tr, ctypes.c_double), _p(tp, ctypes.c_int32), _p(tpe, ctypes.c_int64))
+                            _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double), _p(cover, ctypes.c_int32),
+                            _p(tl, ctypes.c_double), _p(tr, ctypes.c_double), _p(tp, ctypes.c_int32),
+                            _p(tpe, ctypes.c_int64))
     _check(rc, "decode")
-    out = {"u_hat": u_hat, "iters": int(iters[0]), "pe": int(pe[0]), "margin": float(margin[0])}
+    out = {"u_hat": u_hat, "iters": int(iters[0]), "pe": int(pe[0]), "margin": float(margin[0]),
+           "cover": int(cover[0])}
     if trace:
         n = out["iters"]
         out.update(L=tl[:n], R=tr[:n], P=tp[:n], pe_iter=tpe[:n])
@@ -169,8 +175,9 @@ def decode(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_N
 
 
 def decode_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE,
-                 freeze: int = FREEZE_OFF, fp32: bool = False, nthreads: int = 0):
-    """Decode a [batch, N] LLR array; returns (u_hat, iters, pe, margin)."""
+                 freeze: int = FREEZE_OFF, fp32: bool = False, nthreads: int = 0, cover: bool = False):
+    """Decode a [batch, N] LLR array; returns (u_hat, iters, pe, margin), plus the final
+    covered-prefix lengths when ``cover`` is set."""
     frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
     llr = np.ascontiguousarray(llr, dtype=np.float32)
     B, N = llr.shape
@@ -178,11 +185,13 @@ def decode_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = 
     iters = np.zeros(B, np.int32)
     pe = np.zeros(B, np.int64)
     margin = np.zeros(B, np.float64)
+    cv = np.zeros(B, np.int32) if cover else None
     rc = _load().orc_decode_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B, max_iter, alpha,
                                   stop, freeze, 1 if fp32 else 0, nthreads, _p(u_hat, ctypes.c_uint8),
-                                  _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double))
+                                  _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64), _p(margin, ctypes.c_double),
+                                  _p(cv, ctypes.c_int32))
     _check(rc, "decode_batch")
-    return u_hat, iters, pe, margin
+    return (u_hat, iters, pe, margin, cv) if cover else (u_hat, iters, pe, margin)
 
 
 def decode_flood(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE, fp32: bool = False,
@@ -230,6 +239,27 @@ def decode_flood_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: 
                                         _p(margin, ctypes.c_double))
     _check(rc, "decode_flood_batch")
     return u_hat, iters, pe, margin
+
+
+def sc_decode(frozen, llr, exact: bool = True) -> np.ndarray:
+    """Successive-cancellation decision (N,) for one codeword; exact box-plus f or min-sum."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    u_hat = np.zeros(frozen.shape[0], np.uint8)
+    _check(_load().orc_sc_decode(frozen.shape[0], _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float),
+                                 1 if exact else 0, _p(u_hat, ctypes.c_uint8)), "sc_decode")
+    return u_hat
+
+
+def sc_decode_batch(frozen, llr, exact: bool = True, nthreads: int = 0) -> np.ndarray:
+    """Successive-cancellation decisions [batch, N] for a [batch, N] LLR array."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    B, N = llr.shape
+    u_hat = np.zeros((B, N), np.uint8)
+    _check(_load().orc_sc_decode_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B,
+                                       1 if exact else 0, nthreads, _p(u_hat, ctypes.c_uint8)), "sc_decode_batch")
+    return u_hat
 
 
 def wms_forward(frozen, llr, weights, fp32: bool = False, trace: bool = False):

@@ -395,13 +395,14 @@ static int gmatrix_stop(dec_t* d, int use_store)
  *   u_hat      N output bytes (0/1)
  *   iters      iterations executed; pe = PE updates executed (Sec. IV count)
  *   margin     smallest |value| a hard decision was taken on (may be NULL)
+ *   cover      length of the covered prefix at the end (may be NULL)
  *   trace_L, trace_R   optional max_iter x (m+1) x N planes after each iteration
  *   trace_P    optional max_iter entries: covered-prefix length after each iteration
  *   trace_pe   optional max_iter entries: PE updates in each iteration
  * Returns ORC_OK, or a negative error code.
  */
 int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, double alpha, int stop_mode,
-               int freeze, int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin,
+               int freeze, int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin, int32_t* cover,
                double* trace_L, double* trace_R, int32_t* trace_P, int64_t* trace_pe)
 {
     int m = ilog2_exact(N);
@@ -472,6 +473,7 @@ int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, dou
     if (iters) *iters = t_done;
     if (pe) *pe = d.pe;
     if (margin) *margin = d.margin;
+    if (cover) *cover = covered_prefix(&d);
 out:
     free(d.L);
     free(d.R);
@@ -612,7 +614,7 @@ int orc_decode_flood_batch(int N, const uint8_t* frozen, const float* llr, int b
  * the first nonzero error code met, else ORC_OK. */
 int orc_decode_batch(int N, const uint8_t* frozen, const float* llr, int batch, int max_iter, double alpha,
                      int stop_mode, int freeze, int fp32, int nthreads, uint8_t* u_hat, int32_t* iters,
-                     int64_t* pe, double* margin)
+                     int64_t* pe, double* margin, int32_t* cover)
 {
     if (batch < 0) return ORC_ERR_ARG;
     int err = ORC_OK;
@@ -623,7 +625,97 @@ int orc_decode_batch(int N, const uint8_t* frozen, const float* llr, int batch, 
     for (int c = 0; c < batch; ++c) {
         int r = orc_decode(N, frozen, llr + (size_t)c * (size_t)N, max_iter, alpha, stop_mode, freeze, fp32,
                            u_hat + (size_t)c * (size_t)N, iters ? iters + c : NULL, pe ? pe + c : NULL,
-                           margin ? margin + c : NULL, NULL, NULL, NULL, NULL);
+                           margin ? margin + c : NULL, cover ? cover + c : NULL, NULL, NULL, NULL, NULL);
+        if (r != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            {
+                if (err == ORC_OK) err = r;
+            }
+        }
+    }
+    (void)nthreads;
+    return err;
+}
+
+/*
+ * Successive-cancellation (SC) decoding on the same code (Sec. III compares a
+ * frozen CSFG's decision with SC decoding of its constituent code).  With
+ * x = u F^{(x)m} in natural order, a block of S positions with channel LLRs
+ * lam splits into halves: its first half of u sees x1 = x_left ^ x_right, with
+ * LLRs f(lam[t], lam[t + S/2]); once that half is decided (its encoding x1),
+ * the second half sees x2 = x_right = x_left ^ x1, with LLRs
+ * lam[t + S/2] + (1 - 2 x1[t]) lam[t]; the block's encoding is (x1 ^ x2, x2).
+ * A frozen position decides 0, an information position HD(LLR) (values >= 0
+ * decide 0).  f is the exact box-plus (exact != 0), 2 atanh(tanh(a/2) tanh(b/2)),
+ * or its min-sum approximation sign(a) sign(b) min(|a|, |b|).  FP64.  The exact
+ * f is evaluated as written while min(|a|, |b|) < 4 (tanh is not saturated
+ * there, and tiny results keep their relative precision), else as
+ *   sign(a) sign(b) min(|a|, |b|) + log(1 + e^-|a+b|) - log(1 + e^-|a-b|),
+ * the same function, whose correction terms are then small (no cancellation).
+ */
+static double sc_f(int exact, double a, double b)
+{
+    const double mn = fmin(fabs(a), fabs(b));
+    if (!exact) return sgn(a) * sgn(b) * mn;
+    if (mn < 4.0) return 2.0 * atanh(tanh(0.5 * a) * tanh(0.5 * b));
+    return sgn(a) * sgn(b) * mn + log1p(exp(-fabs(a + b))) - log1p(exp(-fabs(a - b)));
+}
+
+/* Decode the block of S positions starting at source index `base` from LLRs
+ * lam[0..S); writes u_hat[base..base+S) and the block's encoding x[0..S).
+ * work holds at least 2 S doubles. */
+static void sc_node(int S, int base, const double* lam, const uint8_t* frozen, int exact, uint8_t* u_hat,
+                    uint8_t* x, double* work)
+{
+    if (S == 1) {
+        uint8_t b = frozen[base] ? 0 : (lam[0] < 0.0 ? 1 : 0);
+        u_hat[base] = b;
+        x[0] = b;
+        return;
+    }
+    const int h = S / 2;
+    double* child = work;   /* h LLRs for the child being decoded */
+    double* rest = work + h; /* scratch for the child's own recursion */
+    for (int t = 0; t < h; ++t) child[t] = sc_f(exact, lam[t], lam[t + h]);
+    sc_node(h, base, child, frozen, exact, u_hat, x, rest);
+    for (int t = 0; t < h; ++t) child[t] = lam[t + h] + (1.0 - 2.0 * (double)x[t]) * lam[t];
+    sc_node(h, base + h, child, frozen, exact, u_hat, x + h, rest);
+    for (int t = 0; t < h; ++t) x[t] ^= x[t + h];
+}
+
+int orc_sc_decode(int N, const uint8_t* frozen, const float* llr, int exact, uint8_t* u_hat)
+{
+    int m = ilog2_exact(N);
+    if (m < 0 || !frozen || !llr || !u_hat) return ORC_ERR_ARG;
+    double* lam = (double*)malloc(sizeof(double) * (size_t)N);
+    double* work = (double*)malloc(sizeof(double) * (size_t)(2 * N + 2));
+    uint8_t* x = (uint8_t*)malloc((size_t)N);
+    int rc = ORC_OK;
+    if (!lam || !work || !x) {
+        rc = ORC_ERR_NOMEM;
+    } else {
+        for (int i = 0; i < N; ++i) lam[i] = (double)llr[i];
+        sc_node(N, 0, lam, frozen, exact, u_hat, x, work);
+    }
+    free(lam);
+    free(work);
+    free(x);
+    return rc;
+}
+
+int orc_sc_decode_batch(int N, const uint8_t* frozen, const float* llr, int batch, int exact, int nthreads,
+                        uint8_t* u_hat)
+{
+    if (batch < 0) return ORC_ERR_ARG;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (int c = 0; c < batch; ++c) {
+        int r = orc_sc_decode(N, frozen, llr + (size_t)c * (size_t)N, exact, u_hat + (size_t)c * (size_t)N);
         if (r != ORC_OK) {
 #ifdef _OPENMP
 #pragma omp critical

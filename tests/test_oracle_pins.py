@@ -492,3 +492,79 @@ def test_reading_b_covers_at_least_reading_a_in_iteration_1(N):
         a = O.decode(fz, llr[c], 1, freeze=O.FREEZE_CSFG, trace=True)
         b = O.decode(fz, llr[c], 1, freeze=O.FREEZE_CSFG_MULTI, trace=True)
         assert int(b["P"][0]) >= int(a["P"][0])
+
+
+# --------------------------------------------------------------------------
+# Successive-cancellation decoding (the cross-check of Sec. III's comparison
+# between a frozen CSFG's decision and SC decoding of its constituent code)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [8, 64, 1024])
+@pytest.mark.parametrize("exact", [True, False])
+def test_sc_noiseless(N, exact):
+    for frac in (0.25, 0.5, 0.75):
+        fz = O.bec_frozen(N, int(N * frac))
+        u = I.info_bits(13, np.arange(4), fz)
+        llr = I.noiseless_llr(O.encode(u), 2.5)
+        assert np.array_equal(O.sc_decode_batch(fz, llr, exact), u)
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_sc_n2_closed_forms(exact):
+    """N = 2, x = (u0 ^ u1, u1): u0 = HD(f(y0, y1)) (the sign of f is sign(y0) sign(y1) for both f),
+    then u1 = HD(y1 + (1 - 2 u0) y0); with u0 frozen, u1 = HD(y0 + y1)."""
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        y = rng.normal(0, 2, 2).astype(np.float32)
+        y0, y1 = float(y[0]), float(y[1])
+        if min(abs(y0), abs(y1), abs(y0 + y1), abs(y1 - y0)) < 1e-6:
+            continue
+        u0 = int((np.sign(y0) * np.sign(y1)) < 0)
+        u1 = int(y1 + (1 - 2 * u0) * y0 < 0)
+        assert O.sc_decode(np.array([0, 0], np.uint8), y, exact).tolist() == [u0, u1]
+        assert O.sc_decode(np.array([1, 0], np.uint8), y, exact).tolist() == [0, int(y0 + y1 < 0)]
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_sc_rate_one_is_reencoded_hard_decision(exact):
+    """With no frozen position every split keeps the hard decisions of its inputs (the sign of f is
+    the xor of the signs, and g keeps the sign of its right input), so u_hat = HD(y) F^{(x)m}."""
+    rng = np.random.default_rng(5)
+    N = 64
+    fz = np.zeros(N, np.uint8)
+    y = rng.normal(0, 2, (50, N)).astype(np.float32)
+    hd = (y < 0).astype(np.uint8)
+    assert np.array_equal(O.sc_decode_batch(fz, y, exact), O.encode(hd))
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_sc_repetition_code_is_ml(exact):
+    """Only the last position carries information: every earlier bit decides 0, each g then adds
+    the two halves, and the last bit decides on the sign of the sum of all LLRs (the ML decision)."""
+    rng = np.random.default_rng(6)
+    for N in (4, 16, 128):
+        fz = np.ones(N, np.uint8)
+        fz[-1] = 0
+        y = rng.normal(0.3, 2, (40, N)).astype(np.float32)
+        s = y.astype(np.float64).sum(axis=1)
+        keep = np.abs(s) > 1e-4
+        out = O.sc_decode_batch(fz, y[keep], exact)
+        assert np.array_equal(out[:, -1], (s[keep] < 0).astype(np.uint8)) and not out[:, :-1].any()
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_sc_exact_first_decision_is_bitwise_map(N):
+    """With the exact f and no frozen position, the first leaf's LLR is the bitwise MAP LLR of u0 with
+    every later bit uniform: log sum_{u: u0=0} P(y|x(u)) / sum_{u: u0=1} P(y|x(u)), x(u) = u F^{(x)m}."""
+    rng = np.random.default_rng(7)
+    fz = np.zeros(N, np.uint8)
+    words = np.array(list(itertools.product([0, 1], repeat=N)), np.uint8)
+    xs = O.encode(words).astype(np.float64)
+    for _ in range(100):
+        y = rng.normal(0, 1.5, N).astype(np.float32)
+        # log P(y | x) up to a constant: sum_i (1 - 2 x_i) y_i / 2
+        ll = ((1 - 2 * xs) * y.astype(np.float64)).sum(axis=1) / 2
+        l0 = np.logaddexp.reduce(ll[words[:, 0] == 0])
+        l1 = np.logaddexp.reduce(ll[words[:, 0] == 1])
+        if abs(l0 - l1) < 1e-6:
+            continue
+        assert O.sc_decode(fz, y, True)[0] == int(l0 < l1)
