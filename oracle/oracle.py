@@ -66,12 +66,14 @@ def _load():
         lib.orc_decode_flood_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, ci, u8p, i32p, i64p, f64p]
         lib.orc_sc_decode.argtypes = [ci, u8p, f32p, ci, u8p]
         lib.orc_sc_decode_batch.argtypes = [ci, u8p, f32p, ci, ci, ci, u8p]
+        lib.orc_decode_q.argtypes = [ci, u8p, f32p, ci, ci, ci, ci, u8p, i32p, i64p, i32p, i32p]
+        lib.orc_decode_q_batch.argtypes = [ci, u8p, f32p, ci, ci, ci, ci, ci, ci, u8p, i32p, i64p]
         lib.orc_max_threads.argtypes = []
         lib.orc_wms_forward.argtypes = [ci, u8p, f32p, ci, f64p, ci, f64p, f64p, f64p]
         lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, f64p, f64p]
         for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
                    "orc_decode_batch", "orc_decode_flood", "orc_decode_flood_batch", "orc_sc_decode",
-                   "orc_sc_decode_batch", "orc_max_threads",
+                   "orc_sc_decode_batch", "orc_decode_q", "orc_decode_q_batch", "orc_max_threads",
                    "orc_wms_forward", "orc_wms_backward"):
             getattr(lib, fn).restype = ci
         _lib = lib
@@ -260,6 +262,45 @@ def sc_decode_batch(frozen, llr, exact: bool = True, nthreads: int = 0) -> np.nd
     _check(_load().orc_sc_decode_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B,
                                        1 if exact else 0, nthreads, _p(u_hat, ctypes.c_uint8)), "sc_decode_batch")
     return u_hat
+
+
+def decode_q(frozen, llr, max_iter: int, A: int = 15, F: int = 2, stop: int = STOP_NONE, trace: bool = False) -> dict:
+    """Quantised-message decode of one codeword (16-bit saturating integers, alpha = A/16, F
+    fractional bits of the channel LLRs).  Returns u_hat, iters, pe and, with ``trace``, the
+    integer planes after each iteration ([iters, m+1, N])."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    N = frozen.shape[0]
+    m = N.bit_length() - 1
+    u_hat = np.zeros(N, np.uint8)
+    iters = np.zeros(1, np.int32)
+    pe = np.zeros(1, np.int64)
+    tl = tr = None
+    if trace:
+        tl = np.zeros((max_iter, m + 1, N), np.int32)
+        tr = np.zeros((max_iter, m + 1, N), np.int32)
+    _check(_load().orc_decode_q(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), max_iter, A, F, stop,
+                                _p(u_hat, ctypes.c_uint8), _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64),
+                                _p(tl, ctypes.c_int32), _p(tr, ctypes.c_int32)), "decode_q")
+    out = {"u_hat": u_hat, "iters": int(iters[0]), "pe": int(pe[0])}
+    if trace:
+        n = out["iters"]
+        out.update(L=tl[:n], R=tr[:n])
+    return out
+
+
+def decode_q_batch(frozen, llr, max_iter: int, A: int = 15, F: int = 2, stop: int = STOP_NONE, nthreads: int = 0):
+    """Quantised-message decode of a [batch, N] LLR array; returns (u_hat, iters, pe)."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    B, N = llr.shape
+    u_hat = np.zeros((B, N), np.uint8)
+    iters = np.zeros(B, np.int32)
+    pe = np.zeros(B, np.int64)
+    _check(_load().orc_decode_q_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B, max_iter, A, F,
+                                      stop, nthreads, _p(u_hat, ctypes.c_uint8), _p(iters, ctypes.c_int32),
+                                      _p(pe, ctypes.c_int64)), "decode_q_batch")
+    return u_hat, iters, pe
 
 
 def wms_forward(frozen, llr, weights, fp32: bool = False, trace: bool = False):

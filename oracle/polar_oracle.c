@@ -729,6 +729,122 @@ int orc_sc_decode_batch(int N, const uint8_t* frozen, const float* llr, int batc
     return err;
 }
 
+/*
+ * Quantised messages (a variant for fixed-point hardware, which Sec. V names as
+ * future work): Eq. (1) under the sweep schedule of R1 with 16-bit saturating
+ * integer messages.
+ *   quantisation   q = clamp(rint(llr * 2^F), -QMAX, QMAX), QMAX = 32767
+ *   saturation     every sum is clamped to [-QMAX, QMAX]; +-QMAX plays +-inf
+ *   scaling        alpha = A / 16 (A in 1..16), f(x, y) = sign(x) sign(y) ((A min(|x|, |y|) + 8) >> 4),
+ *                  the scaled magnitude rounded to the nearest integer (ties up)
+ *   prior          L[m] = +QMAX on frozen positions, 0 elsewhere; interior messages start at 0
+ * Stop, output and PE count are those of the sweep without freezing.  Every
+ * value is an exact integer, so a GPU kernel reproduces it bit for bit.
+ */
+#define QMAX 32767
+
+static int32_t q_sat(int64_t v) { return (int32_t)(v > QMAX ? QMAX : (v < -QMAX ? -QMAX : v)); }
+
+static int32_t q_f(int A, int32_t x, int32_t y)
+{
+    const int32_t ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+    const int32_t mag = ((int32_t)A * (ax < ay ? ax : ay) + 8) >> 4; /* rounded to nearest, ties up */
+    return ((x < 0) != (y < 0)) ? -mag : mag;
+}
+
+int orc_decode_q(int N, const uint8_t* frozen, const float* llr, int max_iter, int A, int F, int stop_mode,
+                 uint8_t* u_hat, int32_t* iters, int64_t* pe, int32_t* trace_L, int32_t* trace_R)
+{
+    int m = ilog2_exact(N);
+    if (m < 1 || !frozen || !llr || max_iter < 1 || A < 1 || A > 16 || F < 0 || F > 8 || !u_hat) return ORC_ERR_ARG;
+    size_t planes = (size_t)(m + 1) * (size_t)N;
+    int32_t* L = (int32_t*)calloc(planes, sizeof(int32_t));
+    int32_t* R = (int32_t*)calloc(planes, sizeof(int32_t));
+    uint8_t* ub = (uint8_t*)malloc((size_t)N);
+    uint8_t* xb = (uint8_t*)malloc((size_t)N);
+    uint8_t* sc = (uint8_t*)malloc((size_t)N);
+    int rc = ORC_OK;
+    if (!L || !R || !ub || !xb || !sc) {
+        rc = ORC_ERR_NOMEM;
+        goto out;
+    }
+    for (int i = 0; i < N; ++i) {
+        double v = rint((double)llr[i] * ldexp(1.0, F));
+        R[i] = q_sat((int64_t)fmax(fmin(v, 1e9), -1e9));
+        L[(size_t)m * N + i] = frozen[i] ? QMAX : 0;
+    }
+    int t_done = max_iter;
+    int64_t count = 0;
+    for (int t = 1; t <= max_iter; ++t) {
+        for (int s = 0; s < m; ++s) {
+            const int h = 1 << (m - 1 - s);
+            for (int a = 0; a < N; ++a) {
+                if (a & h) continue;
+                const int b = a + h;
+                const int32_t La = L[(size_t)(s + 1) * N + a], Lb = L[(size_t)(s + 1) * N + b];
+                const int32_t Ra = R[(size_t)s * N + a], Rb = R[(size_t)s * N + b];
+                const int32_t tt = q_sat((int64_t)Lb + Rb);
+                const int32_t g = q_f(A, La, Ra);
+                L[(size_t)s * N + a] = q_f(A, La, tt);
+                L[(size_t)s * N + b] = q_sat((int64_t)Lb + g);
+                R[(size_t)(s + 1) * N + a] = q_f(A, Ra, tt);
+                R[(size_t)(s + 1) * N + b] = q_sat((int64_t)Rb + g);
+                count += 1;
+            }
+        }
+        if (trace_L) memcpy(trace_L + (size_t)(t - 1) * planes, L, planes * sizeof(int32_t));
+        if (trace_R) memcpy(trace_R + (size_t)(t - 1) * planes, R, planes * sizeof(int32_t));
+        if (stop_mode == 1) {
+            for (int i = 0; i < N; ++i)
+                ub[i] = frozen[i] ? 0 : (q_sat((int64_t)R[(size_t)m * N + i] + L[(size_t)m * N + i]) < 0);
+            polar_transform(ub, xb, N, sc);
+            int same = 1;
+            for (int i = 0; i < N; ++i)
+                if ((q_sat((int64_t)R[i] + L[i]) < 0) != xb[i]) same = 0;
+            if (same) {
+                t_done = t;
+                break;
+            }
+        }
+    }
+    for (int i = 0; i < N; ++i)
+        u_hat[i] = frozen[i] ? 0 : (q_sat((int64_t)R[(size_t)m * N + i] + L[(size_t)m * N + i]) < 0);
+    if (iters) *iters = t_done;
+    if (pe) *pe = count;
+out:
+    free(L);
+    free(R);
+    free(ub);
+    free(xb);
+    free(sc);
+    return rc;
+}
+
+int orc_decode_q_batch(int N, const uint8_t* frozen, const float* llr, int batch, int max_iter, int A, int F,
+                       int stop_mode, int nthreads, uint8_t* u_hat, int32_t* iters, int64_t* pe)
+{
+    if (batch < 0) return ORC_ERR_ARG;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+#endif
+    for (int c = 0; c < batch; ++c) {
+        int r = orc_decode_q(N, frozen, llr + (size_t)c * (size_t)N, max_iter, A, F, stop_mode,
+                             u_hat + (size_t)c * (size_t)N, iters ? iters + c : NULL, pe ? pe + c : NULL, NULL, NULL);
+        if (r != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            {
+                if (err == ORC_OK) err = r;
+            }
+        }
+    }
+    (void)nthreads;
+    return err;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -568,3 +568,55 @@ def test_sc_exact_first_decision_is_bitwise_map(N):
         if abs(l0 - l1) < 1e-6:
             continue
         assert O.sc_decode(fz, y, True)[0] == int(l0 < l1)
+
+
+# --------------------------------------------------------------------------
+# Quantised messages (16-bit saturating integers; a variant for fixed-point hardware)
+# --------------------------------------------------------------------------
+def test_quantised_n2_hand_trace():
+    """(2,1) code, frozen {0}, llr = (1.3, -0.7), F = 2: q = (rint(5.2), rint(-2.8)) = (5, -3),
+    L[1] = (32767, 0).  The one PE (A = 15, f = sign sign ((15 min + 8) >> 4)): t = 0 + (-3) = -3,
+    g = f(32767, 5) = (75 + 8) >> 4 = 5, L[0] = (f(32767, -3), 0 + 5) = (-(53 >> 4), 5) = (-3, 5),
+    R[1] = (f(5, -3), -3 + 5) = (-3, 2); u_1 = HD(2 + 0) = 0.  Both iterations are the same."""
+    r = O.decode_q(np.array([1, 0], np.uint8), np.array([1.3, -0.7], np.float32), 2, A=15, F=2, trace=True)
+    for t in range(2):
+        assert r["R"][t].tolist() == [[5, -3], [-3, 2]]
+        assert r["L"][t].tolist() == [[-3, 5], [32767, 0]]
+    assert r["u_hat"].tolist() == [0, 0] and r["pe"] == 2 and r["iters"] == 2
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_quantised_matches_float_decoder_without_rounding(N):
+    """alpha = 1 (A = 16: (16 min + 8) >> 4 = min) on integer channel values with F = 0 and no
+    saturation: every message is the float decoder's (the oracle's FP64 sweep), reading the
+    saturated side (|q| > 16384, built from the +32767 prior) as the float decoder's +-inf."""
+    rng = np.random.default_rng(8)
+    fz = O.bec_frozen(N, N // 2)
+    for _ in range(40):
+        y = rng.integers(-20, 21, N).astype(np.float32)
+        q = O.decode_q(fz, y, 6, A=16, F=0, trace=True)
+        f = O.decode(fz, y, 6, alpha=1.0, trace=True)
+        for key in ("L", "R"):
+            qv = q[key].astype(np.float64)
+            qv[qv > 16384] = np.inf
+            qv[qv < -16384] = -np.inf
+            assert np.array_equal(qv, f[key])
+        assert np.array_equal(q["u_hat"], f["u_hat"])
+
+
+@pytest.mark.parametrize("N", [8, 64, 1024])
+def test_quantised_noiseless_stops_in_iteration_1(N):
+    m = N.bit_length() - 1
+    fz = O.bec_frozen(N, N // 2)
+    u = I.info_bits(14, np.arange(4), fz)
+    llr = I.noiseless_llr(O.encode(u), 2.5)
+    uh, it, pe = O.decode_q_batch(fz, llr, 20, 15, 3, O.STOP_GMATRIX)
+    assert np.array_equal(uh, u) and np.all(it == 1) and np.all(pe == m * N // 2)
+
+
+def test_quantised_channel_values():
+    """R[0] is clamp(rint(llr 2^F), -32767, 32767), with rint rounding half to even."""
+    llr = np.array([0.3125, -0.3125, 1.0625, 2.9, -5000.0, 5000.0, 0.0, -0.0], np.float32)
+    r = O.decode_q(np.zeros(8, np.uint8), llr, 1, A=15, F=3, trace=True)
+    want = np.clip(np.rint(llr.astype(np.float64) * 8), -32767, 32767).astype(np.int64)
+    assert r["R"][0][0].tolist() == want.tolist() == [2, -2, 8, 23, -32767, 32767, 0, 0]
