@@ -681,6 +681,61 @@ def run_readings(args):
     return 0
 
 
+def run_quantized(args):
+    """Quantised 16-bit messages (fixed-point variant) against binary32 messages on the same
+    (1024,512) codewords at 2.5 and 3.0 dB, G-matrix stop, max 60 iterations, alpha 0.9375 (A = 15),
+    2, 3 and 5 fractional bits: FER with Wilson 95 % intervals, iterations and info Gbit/s."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n_cw = 1 << 20
+    code = B.polarbp_construct(N, K)
+    uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
+    it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
+    pe = torch.empty(n_cw, dtype=torch.int64, device="cuda")
+    points = []
+    with ClockSampler(0) as clk:
+        for eb in (2.5, 3.0):
+            u, llr = B.polarbp_awgn(code, SEED + 17, 0, n_cw, eb)
+            row = {"ebn0_db": eb, "codewords": n_cw}
+            variants = [("binary32", None)] + [(f"int16_F{f}", f) for f in (2, 3, 5)]
+            for name, F in variants:
+                def call():
+                    if F is None:
+                        B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, 0, uh, it, pe, stream=stream)
+                    else:
+                        B.polarbp_decode_quantized(code, llr, MAX_ITER, 15, F, 1, uh, it, pe, stream=stream)
+                call()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                errs = int((uh != u).any(dim=1).sum().item())
+                pe_sum = float(pe.double().sum().item())
+                row[name] = {"fer": errs / n_cw, "fer_ci95": list(wilson(errs, n_cw)),
+                             "avg_iters": float(it.double().mean().item()), "ms": ms,
+                             "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9,
+                             "pe_per_s": pe_sum / (ms * 1e-3), "alu_frac": pe_sum / (ms * 1e-3) / PEAK_PE_PER_S}
+            points.append(row)
+            del u, llr
+            torch.cuda.empty_cache()
+    head = next(p for p in points if p["ebn0_db"] == 3.0)["int16_F3"]
+    line = {"metric": "info Gbit/s/GB300, 16-bit quantised messages vs binary32, (1024,512), G-matrix stop",
+            "unit": "Gbit/s", "value": head["info_gbit_s"], "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+            "config": {"workload": f"(1024,512) code, {n_cw} codewords per point, alpha 15/16, max 60 iterations, "
+                                   "G-matrix stop, device generator"},
+            "points": points, "clocks": clk.summary(), "gpu_launches": 2 * 4 * len(points)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_long(args):
     """Long codes: N in {8192, 16384, 32768}, K = N/2, Eb/N0 in {2.0, 2.5, 3.0} dB, 10^5
     codewords per point (device generator), G-matrix stop + CSFG freezing, at most 100
@@ -884,11 +939,13 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--sweep-codewords", type=int, default=1000000)
-    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms", "sweep", "flooding", "readings"],
+    ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms", "sweep", "flooding", "readings",
+                                           "quantized"],
                     default="n1024",
                     help="n1024: the (1024,512) headline; mixed: the mixed-length stream; long: N = 8192..32768 "
                          "on thread-block clusters; wms: learned weights; sweep: FER over Eb/N0; flooding: the "
-                         "true flooding schedule against the sweep; readings: freezing order A against B")
+                         "true flooding schedule against the sweep; readings: freezing order A against B; "
+                         "quantized: 16-bit messages against binary32")
     ap.add_argument("--long-codewords", type=int, default=100000)
     ap.add_argument("--long-n", type=int, default=0, help="one code length of the long workload (default: all)")
     ap.add_argument("--long-ebn0", type=float, default=None, help="one Eb/N0 point of the long workload")
@@ -908,6 +965,8 @@ def main():
         return run_flooding(args)
     if args.workload == "readings":
         return run_readings(args)
+    if args.workload == "quantized":
+        return run_quantized(args)
     if args.workload == "sweep":
         return run_sweep(args)
     return run_ours(args)

@@ -183,6 +183,32 @@ int polarbp_decode_flooding(const polarbp_code* code, const float* llr, int batc
                             float* trace_L, float* trace_R, void* stream);
 
 /*
+ * polarbp_decode_quantized -- BP decoding with quantised messages, a variant
+ * for fixed-point hardware (Sec. V names a VLSI architecture as future work).
+ * Eq. (1) under the sweep schedule of polarbp_decode, without freezing, with
+ * 16-bit saturating integer messages in [-32767, 32767]:
+ *   channel values  q = clamp(rint(llr * 2^frac_bits)), round half to even;
+ *   sums            clamped to the range, whose ends stand for +-inf;
+ *   scaling         alpha = alpha_16 / 16, f(x, y) =
+ *                   sign(x) sign(y) ((alpha_16 min(|x|, |y|) + 8) >> 4);
+ *   prior           +32767 on frozen positions, 0 elsewhere.
+ *   llr, batch, max_iter, stop_mode, u_hat, iterations, pe_updates
+ *                    as polarbp_decode (stop_mode NONE or GMATRIX;
+ *                    pe_updates = iterations m N/2).
+ *   alpha_16         1..16 (15 gives the paper's 0.9375).
+ *   frac_bits        0..8 fractional bits of the channel values.
+ *   trace_L, trace_R NULL, or both [batch][max_iter][m+1][N] int16 device
+ *                    buffers receiving the planes after every iteration.
+ * N <= 1024 (the int16 planes of a codeword, 4 (m+1) N bytes, sit in shared
+ * memory).  Every value is an exact integer.  Non-finite LLRs are recorded in
+ * the status word.  Errors: POLARBP_ERR_ARG, POLARBP_ERR_UNSUPPORTED,
+ * POLARBP_ERR_CUDA.
+ */
+int polarbp_decode_quantized(const polarbp_code* code, const float* llr, int batch, int max_iter, int alpha_16,
+                             int frac_bits, int stop_mode, uint8_t* u_hat, int32_t* iterations,
+                             int64_t* pe_updates, int16_t* trace_L, int16_t* trace_R, void* stream);
+
+/*
  * polarbp_decode_host_workspace -- bytes of device workspace polarbp_decode_host
  * needs for `batch` codewords (256-byte aligned sub-buffers).
  */

@@ -53,6 +53,8 @@ _SIGS = {
                                             ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "polarbp_decode_flooding": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                                _VP, _VP, _VP, _VP, _VP, _VP]),
+    "polarbp_decode_quantized": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
     "polarbp_decode_host_workspace": (ctypes.c_size_t, [_VP, ctypes.c_int]),
     "polarbp_decode_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                            ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
@@ -319,6 +321,34 @@ def polarbp_decode_flooding(code: PolarCode, llr, max_iter: int, scale: float = 
     _check(lib().polarbp_decode_flooding(code.handle, _ptr(llr), B, max_iter, scale, stop_mode, _ptr(u_hat),
                                          _ptr(iterations), _ptr(pe_updates), _ptr(tl), _ptr(tr), _stream(stream)),
            "polarbp_decode_flooding")
+    return (u_hat, iterations, pe_updates, tl, tr) if trace else (u_hat, iterations, pe_updates)
+
+
+def polarbp_decode_quantized(code: PolarCode, llr, max_iter: int, alpha_16: int = 15, frac_bits: int = 3,
+                             stop_mode: int = 0, u_hat=None, iterations=None, pe_updates=None, trace: bool = False,
+                             stream=None):
+    """Quantised-message decode; returns (u_hat, iterations, pe_updates) or, with ``trace``,
+    (u_hat, iterations, pe_updates, trace_L, trace_R) with int16 planes [batch, max_iter, m+1, N]."""
+    import torch
+    B = llr.shape[0]
+    _need(llr, torch.float32, (B, code.N), "llr")
+    if u_hat is None:
+        u_hat = torch.empty((B, code.N), dtype=torch.uint8, device=llr.device)
+    if iterations is None:
+        iterations = torch.empty(B, dtype=torch.int32, device=llr.device)
+    if pe_updates is None:
+        pe_updates = torch.empty(B, dtype=torch.int64, device=llr.device)
+    _need(u_hat, torch.uint8, (B, code.N), "u_hat")
+    _need(iterations, torch.int32, (B,), "iterations")
+    _need(pe_updates, torch.int64, (B,), "pe_updates")
+    tl = tr = None
+    if trace:
+        m = code.N.bit_length() - 1
+        tl = torch.zeros((B, max_iter, m + 1, code.N), dtype=torch.int16, device=llr.device)
+        tr = torch.zeros_like(tl)
+    _check(lib().polarbp_decode_quantized(code.handle, _ptr(llr), B, max_iter, alpha_16, frac_bits, stop_mode,
+                                          _ptr(u_hat), _ptr(iterations), _ptr(pe_updates), _ptr(tl), _ptr(tr),
+                                          _stream(stream)), "polarbp_decode_quantized")
     return (u_hat, iterations, pe_updates, tl, tr) if trace else (u_hat, iterations, pe_updates)
 
 
