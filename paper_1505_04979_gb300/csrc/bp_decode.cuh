@@ -143,7 +143,6 @@ struct DecodeArgs {
     int batch;
     int max_iter;
     float alpha;
-    int multi;  // reading B: checks continue along a stage while they pass (a variant)
 };
 
 // Pointers of one codeword (trace pointers already offset to the codeword).
@@ -397,10 +396,10 @@ __device__ __forceinline__ void polar_xform(uint32_t (&v)[RW], int S, int lane)
 // take several events in one iteration; they are consecutive CSFGs (P only
 // grows, and by steps no larger than the column's CSFGs), so the range grows.
 template <int M>
-__device__ __forceinline__ void note_event(Smem<M>& sm, int J, int lo, int hi, int lane)
+__device__ __forceinline__ void note_event(Smem<M>& sm, int J, int lo, int hi, int lane, bool multi = false)
 {
     if (lane == 0) {
-        if (!(sm.ctl[CTL_EVENT] & (1 << J))) sm.ev_lo()[J] = lo;
+        if (!multi || !(sm.ctl[CTL_EVENT] & (1 << J))) sm.ev_lo()[J] = lo;
         sm.ev_hi()[J] = hi;
         sm.ctl[CTL_EVENT] |= 1 << J;
     }
@@ -410,7 +409,7 @@ __device__ __forceinline__ void note_event(Smem<M>& sm, int J, int lo, int hi, i
 // has become fully covered: its hard decision is its stored source bits
 // re-encoded (the +-inf messages its own PEs would emit).
 template <int M>
-__device__ __forceinline__ void propagate(Smem<M>& sm, int P, int J, int lane)
+__device__ __forceinline__ void propagate(Smem<M>& sm, int P, int J, int lane, bool multi = false)
 {
     constexpr int N = Geo<M>::N, NW = Geo<M>::NW, RW = Geo<M>::RW;
 #pragma unroll 1
@@ -436,7 +435,7 @@ __device__ __forceinline__ void propagate(Smem<M>& sm, int P, int J, int lane)
             const uint32_t mk = low_mask(Sp) << off;
             xo[bp >> 5] = (xo[bp >> 5] & ~mk) | (v & mk);
         }
-        note_event(sm, jp, bp, P, lane);
+        note_event(sm, jp, bp, P, lane, multi);
         __syncwarp();
     }
 }
@@ -573,9 +572,12 @@ __device__ __forceinline__ void speculate(Smem<M>& sm, Spec<M>& sp, const SpecSl
 // the first pass failed against the frontier they would have seen.  Returns
 // the PE updates of the iteration (Sec. IV count; stage s runs the PEs outside
 // covered CSFGs given P after the check of stage s).
-template <int M>
-__device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane, bool multi)
+// MULTI selects reading B (a variant): after a CSFG of stage J freezes, the next
+// round checks stage J again from the new frontier, on the same R[J].
+template <int M, bool MULTI>
+__device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane)
 {
+    constexpr bool multi = MULTI;
     using SP = Spec<M>;
     constexpr int N = Geo<M>::N, NW = Geo<M>::NW;
     int jmin = 1;
@@ -609,10 +611,10 @@ __device__ __forceinline__ int resolve(Smem<M>& sm, int& P, int lane, bool multi
             // a stage-M CSFG is one position; its feedback goes straight to column M
             if (J == M) sm.Lm[cand] = (sp.xs & 1u) ? -INFINITY : INFINITY;
         }
-        if (J < M) note_event(sm, J, cand, cand + S, lane);
+        if (J < M) note_event(sm, J, cand, cand + S, lane, multi);
         P = cand + S;
         __syncwarp();
-        propagate<M>(sm, P, J, lane);
+        propagate<M>(sm, P, J, lane, multi);
         if (lane >= J) Ps = P;
         jmin = multi ? J : J + 1;  // reading B checks the next CSFG of the same stage, on the same R[J]
     }
@@ -727,8 +729,8 @@ __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
     return __all_sync(kFull, same);
 }
 
-template <int M, bool GSTOP, bool FREEZE>
-__device__ __forceinline__ void checker(unsigned char* smem_base, int lane, bool multi)
+template <int M, bool GSTOP, bool FREEZE, bool MULTI>
+__device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
 {
     constexpr int N = Geo<M>::N;
     Smem<M> sm(smem_base);
@@ -741,7 +743,7 @@ __device__ __forceinline__ void checker(unsigned char* smem_base, int lane, bool
     int P = sm.ctl[CTL_P];
     int pe_it = N >> 1;  // stage 0 always runs
     if constexpr (FREEZE) {
-        pe_it = resolve<M>(sm, P, lane, multi);
+        pe_it = resolve<M, MULTI>(sm, P, lane);
     } else {
         pe_it = M * (N >> 1);
     }
@@ -1117,9 +1119,9 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
 
 // Decode one codeword with the BLOCK threads of group grp (tid = thread index in
 // the group) on the group's shared memory smem_raw.
-template <int M, bool GSTOP, bool FREEZE, bool TRACE, int CPC>
+template <int M, bool GSTOP, bool FREEZE, bool TRACE, int CPC, bool MULTI = false>
 __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, float alpha, unsigned int* status,
-                                                unsigned char* smem_raw, int tid, int grp, bool multi = false)
+                                                unsigned char* smem_raw, int tid, int grp)
 {
     using G = Geo<M>;
     constexpr int N = G::N, EL = G::EL, T = G::T, NW = G::NW;
@@ -1178,7 +1180,7 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
         group_sync<G::BLOCK, CPC>(grp);
         bool done = false;
         if constexpr (GSTOP || FREEZE) {
-            if (tid < 32) checker<M, GSTOP, FREEZE>(smem_raw, lane, multi);
+            if (tid < 32) checker<M, GSTOP, FREEZE, MULTI>(smem_raw, lane);
             group_sync<G::BLOCK, CPC>(grp);
             done = sm.ctl[CTL_DONE] != 0;
             if constexpr (FREEZE) {
@@ -1221,8 +1223,8 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
     }
 }
 
-// One codeword per block, grid = batch.
-template <int M, bool GSTOP, bool FREEZE, bool TRACE>
+// One codeword per block, grid = batch.  MULTI: freezing under reading B.
+template <int M, bool GSTOP, bool FREEZE, bool TRACE, bool MULTI = false>
 __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::min_blocks(FREEZE)) bp_decode_kernel(DecodeArgs a)
 {
     constexpr int N = Geo<M>::N;
@@ -1237,8 +1239,7 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::min_blocks(FREEZE)) bp_
                   TRACE ? a.trace_L + tb : nullptr,
                   TRACE ? a.trace_R + tb : nullptr,
                   TRACE ? a.trace_P + cw * a.max_iter : nullptr};
-    decode_codeword<M, GSTOP, FREEZE, TRACE, 1>(io, a.max_iter, a.alpha, a.status, smem_raw, threadIdx.x, 0,
-                                                a.multi != 0);
+    decode_codeword<M, GSTOP, FREEZE, TRACE, 1, MULTI>(io, a.max_iter, a.alpha, a.status, smem_raw, threadIdx.x, 0);
 }
 
 // Persistent decoding of a queue of codewords split in segments (one code per
@@ -1310,10 +1311,10 @@ struct LaunchReq {
     cudaStream_t stream;
 };
 
-template <int M, bool GSTOP, bool FREEZE, bool TRACE>
+template <int M, bool GSTOP, bool FREEZE, bool TRACE, bool MULTI = false>
 cudaError_t launch_one(const LaunchReq& q)
 {
-    auto kern = bp_decode_kernel<M, GSTOP, FREEZE, TRACE>;
+    auto kern = bp_decode_kernel<M, GSTOP, FREEZE, TRACE, MULTI>;
     constexpr size_t smem = SmemLayout<M>::bytes;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1327,6 +1328,10 @@ template <int M>
 cudaError_t launch_decode(const LaunchReq& q)
 {
     const bool g = q.stop_mode != 0, f = q.freeze_mode != 0;
+    if (q.freeze_mode == 2) {  // reading B
+        if (q.trace) return g ? launch_one<M, true, true, true, true>(q) : launch_one<M, false, true, true, true>(q);
+        return g ? launch_one<M, true, true, false, true>(q) : launch_one<M, false, true, false, true>(q);
+    }
     if (q.trace) {
         if (g && f) return launch_one<M, true, true, true>(q);
         if (g) return launch_one<M, true, false, true>(q);

@@ -259,7 +259,6 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     q.args.batch = batch;
     q.args.max_iter = max_iter;
     q.args.alpha = scale;
-    q.args.multi = freeze_mode == POLARBP_FREEZE_CSFG_MULTI ? 1 : 0;
     q.stop_mode = stop_mode;
     q.freeze_mode = freeze_mode;
     q.trace = trace;
