@@ -141,12 +141,17 @@ def barrier(world):
         dist.barrier()
 
 
+def _reduce_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(x: float, world: int) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -156,9 +161,15 @@ def sum_over_ranks(v, world):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor(v, dtype=torch.float64, device="cuda")
+    t = torch.tensor(v, dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return t.tolist()
+
+
+def shard_first(rank: int, batch: int) -> int:
+    """First codeword index of a rank: codewords are independent and the keyed generator
+    regenerates any of them, so rank r decodes [r * batch, (r + 1) * batch) (weak scaling)."""
+    return rank * batch
 
 
 # ---------------------------------------------------------------------------
@@ -289,7 +300,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     batch = args.batch
     code = B.polarbp_construct(N, K)
-    first = rank * batch
+    first = shard_first(rank, batch)
     u, llr = B.polarbp_awgn(code, SEED, first, batch, EBN0)
     uh = torch.empty((batch, N), dtype=torch.uint8, device="cuda")
     it = torch.empty(batch, dtype=torch.int32, device="cuda")
