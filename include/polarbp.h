@@ -34,11 +34,11 @@ typedef enum polarbp_status {
     POLARBP_ERR_ARG = 1,         /* an argument is out of range or NULL where not allowed */
     POLARBP_ERR_NONFINITE = 2,   /* a decode saw a NaN or infinite channel LLR */
     POLARBP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
-    POLARBP_ERR_TIMEOUT = 4,     /* reserved for a device-side bounded wait; no kernel in this build
+    POLARBP_ERR_TIMEOUT = 4,     /* reserved for a device-side bounded wait; no kernel of the library
                                     spins on a flag (work queues use atomics, the cluster decoder
                                     hardware cluster barriers), so no call returns it */
     POLARBP_ERR_NOMEM = 5,       /* a library allocation failed */
-    POLARBP_ERR_UNSUPPORTED = 6  /* valid arguments this build has no kernel for */
+    POLARBP_ERR_UNSUPPORTED = 6  /* valid arguments the library has no kernel for */
 } polarbp_status;
 
 typedef enum polarbp_stop_mode {

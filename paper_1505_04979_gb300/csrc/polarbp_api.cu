@@ -242,7 +242,7 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     if (batch == 0) return POLARBP_OK;
     if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be device pointers");
     if (trace && (!trace_L || !trace_R || !trace_P)) return fail(POLARBP_ERR_ARG, "trace buffers must be given");
-    if (c->m > 15) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 32768 in this build");
+    if (c->m > 15) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 32768");
     int rc = check_device(c);
     if (rc != POLARBP_OK) return rc;
 
