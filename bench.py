@@ -644,7 +644,7 @@ def run_flooding(args):
 
 def run_readings(args):
     """The freezing order of Sec. III under reading A (one check per stage per iteration, the
-    build's reading) and reading B (checks continue along a stage while they pass), with the
+    decoder's default) and reading B (checks continue along a stage while they pass), with the
     G-matrix stop, on the same (1024,512) codewords at 2.5, 3.0 and 3.5 dB, max 60 iterations:
     FER with Wilson 95 % intervals, iterations, PE updates per codeword and info Gbit/s."""
     import torch
