@@ -83,7 +83,8 @@ int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polar
 int polarbp_frozen_set(int N, int K, double z0, uint8_t* frozen_mask);
 
 /* polarbp_destroy -- release a handle (NULL is ignored).  Synchronises the
- * device before freeing its tables, streams and events. */
+ * handle's device (making it current for the call and restoring the caller's
+ * device afterwards) before freeing its tables, streams and events. */
 void polarbp_destroy(polarbp_code* code);
 
 /* polarbp_code_info -- N, K and m = log2 N of a handle (any out pointer may be NULL). */
@@ -318,6 +319,8 @@ size_t polarbp_decode_segments_workspace(void);
  *   workspace    device buffer of polarbp_decode_segments_workspace() bytes
  *                (counters; zeroed by the call).  Calls sharing a workspace must
  *                not overlap on the GPU.
+ * A non-finite LLR sets the status word of its own segment's code (read with
+ * polarbp_get_status on that code).
  * Errors: POLARBP_ERR_ARG, POLARBP_ERR_UNSUPPORTED (N < 256 or > 4096), POLARBP_ERR_CUDA.
  */
 int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,

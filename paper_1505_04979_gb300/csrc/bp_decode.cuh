@@ -1253,8 +1253,8 @@ struct SegArgs {
     int* queue;  // device counter, zero at launch
     int max_iter;
     float alpha;
-    unsigned int* status;
     int start[kMaxSeg + 1];  // first queue index of each segment; start[nseg] = total
+    unsigned int* status[kMaxSeg];  // the status word of each segment's code
     const float* llr[kMaxSeg];
     const uint32_t* frozen_words[kMaxSeg];
     uint8_t* u_hat[kMaxSeg];
@@ -1298,7 +1298,7 @@ __global__ void __launch_bounds__(PersistentShape<M, CPC>::THREADS, PersistentSh
                       nullptr,
                       nullptr,
                       nullptr};
-        decode_codeword<M, GSTOP, FREEZE, false, CPC>(io, a.max_iter, a.alpha, a.status, smem, tid, grp);
+        decode_codeword<M, GSTOP, FREEZE, false, CPC>(io, a.max_iter, a.alpha, a.status[sg], smem, tid, grp);
     }
 }
 

@@ -314,7 +314,18 @@ int side_resources(SideResources** out)
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.join[k], cudaEventDisableTiming);
         }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "side stream creation");
+        if (e != cudaSuccess) {
+            // undo a partial creation so that the next call starts clean
+            for (int k = 0; k < kSideStreams; ++k) {
+                if (r.side[k]) cudaStreamDestroy(r.side[k]);
+                if (r.join[k]) cudaEventDestroy(r.join[k]);
+                r.side[k] = nullptr;
+                r.join[k] = nullptr;
+            }
+            if (r.fork) cudaEventDestroy(r.fork);
+            r.fork = nullptr;
+            return cuda_fail(e, "side stream creation");
+        }
         r.ready = true;
     }
     *out = &r;
@@ -459,8 +470,14 @@ int polarbp_frozen_set(int N, int K, double z0, uint8_t* frozen_mask)
 void polarbp_destroy(polarbp_code* c)
 {
     if (!c) return;
+    // drain the handle's device, which need not be the caller's current one
+    const int dev = c->device;
+    int cur = -1;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != dev;
+    if (other) cudaSetDevice(dev);
     cudaDeviceSynchronize();
     release(c);
+    if (other) cudaSetDevice(cur);
 }
 
 int polarbp_code_info(const polarbp_code* c, int* N, int* K, int* m)
@@ -703,13 +720,13 @@ int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter,
         q.args.queue = static_cast<int*>(workspace) + m;
         q.args.max_iter = max_iter;
         q.args.alpha = scale;
-        q.args.status = segs[by_m[m][0]].code->d_status;
         int start = 0;
         for (int j = 0; j < q.args.nseg; ++j) {
             const polarbp_segment& sg = segs[by_m[m][j]];
             q.args.start[j] = start;
             q.args.llr[j] = sg.llr;
             q.args.frozen_words[j] = sg.code->d_frozen;
+            q.args.status[j] = sg.code->d_status;
             q.args.u_hat[j] = sg.u_hat;
             q.args.iters[j] = sg.iterations;
             q.args.pe[j] = sg.pe_updates;

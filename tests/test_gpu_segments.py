@@ -140,3 +140,16 @@ def test_mixed_full_size_sampled(B):
         assert np.array_equal(uh[sel].cpu().numpy(), ouh)
         assert np.array_equal(it[sel].cpu().numpy(), oit)
         assert np.array_equal(pe[sel].cpu().numpy(), ope)
+
+
+def test_nonfinite_input_reported_on_its_own_code(B):
+    """Two runs of the same length with different codes: a NaN in the second run's LLRs sets
+    the status word of the second code only."""
+    c1, c2 = B.polarbp_construct(1024, 512), B.polarbp_construct(1024, 256)
+    l1 = class_inputs(1024, 512, np.arange(8), 9)[1]
+    l2 = class_inputs(1024, 256, np.arange(8, 16), 9)[1]
+    l2[3, 17] = np.nan
+    assert B.polarbp_get_status(c1) == B.POLARBP_OK and B.polarbp_get_status(c2) == B.POLARBP_OK
+    run_segments(B, [c1, c2], [l1, l2], 20, (1, 1))
+    assert B.polarbp_get_status(c1) == B.POLARBP_OK
+    assert B.polarbp_get_status(c2) == B.POLARBP_ERR_NONFINITE
