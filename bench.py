@@ -369,10 +369,14 @@ def run_ours(args):
         for _ in range(e2e_steps):
             B.polarbp_decode_host(code, h_llr, MAX_ITER, ALPHA, *main, h_u, h_it, h_pe, ws, stream=stream)
         dt = max_over_ranks(time.perf_counter() - t0, world)
-        gpu_launches += e2e_steps
+        # the host entry point decodes a large batch as a pipeline of chunks of 64 MiB of
+        # LLRs, one kernel launch each (a smaller batch is one launch)
+        cb = max(1, (64 << 20) // (N * 4))
+        launches_per_call = -(-batch // cb) if batch >= 2 * cb else 1
         e2e = {"value": batch * world * K * e2e_steps / dt / 1e9, "unit": "Gbit/s",
                "h2d_bytes_per_step": batch * N * 4, "d2h_bytes_per_step": batch * (N + 4 + 8),
-               "steps": e2e_steps, "entry_point": "polarbp_decode_host"}
+               "steps": e2e_steps, "entry_point": "polarbp_decode_host",
+               "gpu_launches": launches_per_call * e2e_steps}
         del h_llr, h_u, h_it, h_pe, ws
 
     if rank != 0:
