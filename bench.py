@@ -564,7 +564,7 @@ def run_flooding(args):
     """True flooding schedule (every PE from the previous iteration's messages) against the
     paper's left-to-right sweep, on the same codewords: the tiny-code configuration ((64,32),
     Eb/N0 2.5 dB, 40 fixed iterations, alpha 0.9375; its 1000-codeword case is a parity test,
-    here 2^20 codewords from the device generator) and (1024,512) at 3.0 dB with the G-matrix
+    here --batch codewords (2^20 by default) from the device generator) and (1024,512) at 3.0 dB with the G-matrix
     stop, max 60 iterations.  FER with Wilson 95 % intervals, average iterations, and info
     Gbit/s timed with CUDA events (K steps after W warm-up steps per line)."""
     import torch
@@ -580,7 +580,7 @@ def run_flooding(args):
     with ClockSampler(0) as clk:
         for name, n, k, eb, iters, stop in cases:
             code = B.polarbp_construct(n, k)
-            n_cw = 1 << 20
+            n_cw = args.batch
             u, llr = B.polarbp_awgn(code, SEED + 11, 0, n_cw, eb)
             uh = torch.empty((n_cw, n), dtype=torch.uint8, device="cuda")
             it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
@@ -636,8 +636,9 @@ def run_flooding(args):
             "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "flooding schedule: (64,32) 2.5 dB 40 fixed iterations and (1024,512) 3.0 dB "
-                                   "G-matrix stop max 60, 2^20 codewords each, alpha 0.9375, device generator",
-                       "l2": "inputs larger than L2 at N=1024 (4 GiB); 256 MiB at N=64"},
+                                   f"G-matrix stop max 60, {args.batch} codewords each, alpha 0.9375, device generator",
+                       "l2": f"LLR inputs of {args.batch * 1024 * 4 >> 20} MiB at N=1024 and "
+                             f"{args.batch * 64 * 4 >> 20} MiB at N=64 (L2 is 129 MB), no flush"},
             "cases": out, "clocks": clk.summary(), "gpu_launches": 2 * len(cases) * (steps + max(1, args.warmup)),
             "cpu_baseline": {"value": n_cpu * 32 / dt / 1e9, "unit": "Gbit/s", "cores": O.max_threads(),
                              "kind": "oracle", "sample": f"{n_cpu} codewords of (64,32) at 2.5 dB, 40 flooding "
@@ -657,7 +658,7 @@ def run_readings(args):
     build.build()
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    n_cw = 1 << 20
+    n_cw = args.batch
     code = B.polarbp_construct(N, K)
     uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
     it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
@@ -706,7 +707,7 @@ def run_quantized(args):
     build.build()
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    n_cw = 1 << 20
+    n_cw = args.batch
     code = B.polarbp_construct(N, K)
     uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
     it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
