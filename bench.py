@@ -564,8 +564,8 @@ def run_flooding(args):
     """True flooding schedule (every PE from the previous iteration's messages) against the
     paper's left-to-right sweep, on the same codewords: the tiny-code configuration ((64,32),
     Eb/N0 2.5 dB, 40 fixed iterations, alpha 0.9375; its 1000-codeword case is a parity test,
-    here --batch codewords (2^20 by default) from the device generator) and (1024,512) at 3.0 dB with the G-matrix
-    stop, max 60 iterations.  FER with Wilson 95 % intervals, average iterations, and info
+    here --batch codewords, 2^20 by default, from the device generator) and (1024,512) at
+    3.0 dB with the G-matrix stop, max 60 iterations.  FER with Wilson 95 % intervals, average iterations, and info
     Gbit/s timed with CUDA events (K steps after W warm-up steps per line)."""
     import torch
     from oracle import oracle as O
