@@ -128,4 +128,4 @@ def test_autograd_function_and_training_step(B):
         l = loss_fn()
         l.backward()
         opt.step()
-    assert float(loss_fn()) < first
+    assert float(loss_fn().detach()) < first
