@@ -213,7 +213,6 @@ __device__ __forceinline__ uint32_t xor_supersets(cg::cluster_group& cl, uint32_
 template <int XC>
 __device__ __forceinline__ void local_stage_checks(Smem<12>& sm, CSmem<XC>& cs, int jl, int lane)
 {
-    constexpr int HDS = Geo<12>::HDS;
     const int S = 1 << (12 - jl);
     uint32_t u[4];
 #pragma unroll
@@ -268,7 +267,6 @@ __device__ __forceinline__ void local_stage_checks(Smem<12>& sm, CSmem<XC>& cs, 
 template <int XC>
 __device__ __forceinline__ void uhat_transform(Smem<12>& sm, int Ploc, uint32_t* dst, int lane)
 {
-    constexpr int HDS = Geo<12>::HDS;
     uint32_t u[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
