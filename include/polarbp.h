@@ -272,9 +272,12 @@ int polarbp_awgn(const polarbp_code* code, uint64_t seed, uint64_t first_codewor
  *   batch must satisfy polarbp_decode_host_workspace(code, batch) <=
  *   POLARBP_NOALLOC_SCRATCH_BYTES (about 3,200 codewords at N = 1024);
  *   larger batches return POLARBP_ERR_ARG with the limit in the message.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and leave the
+ * The current device must be the handle's (POLARBP_ERR_ARG otherwise, before
+ * anything is enqueued).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current and keeps it
+ * for the life of the process; make that first call before any stream capture.
+ * cudaDeviceReset invalidates that address together with every code handle of
+ * the device: after a reset, call nothing in this library on that device.  All calls share the one array and leave the
  * last call's contents in it; nothing in it needs to start at zero (each call
  * writes every byte it reads).  Calls that overlap on the GPU -- on different
  * streams or host threads at the same time on the same device -- race on the

@@ -70,7 +70,7 @@ def _load():
         lib.orc_decode_q_batch.argtypes = [ci, u8p, f32p, ci, ci, ci, ci, ci, ci, u8p, i32p, i64p]
         lib.orc_max_threads.argtypes = []
         lib.orc_wms_forward.argtypes = [ci, u8p, f32p, ci, f64p, ci, f64p, f64p, f64p]
-        lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, f64p, f64p]
+        lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, ci, f64p, f64p]
         for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
                    "orc_decode_batch", "orc_decode_flood", "orc_decode_flood_batch", "orc_sc_decode",
                    "orc_sc_decode_batch", "orc_decode_q", "orc_decode_q_batch", "orc_max_threads",
@@ -322,8 +322,9 @@ def wms_forward(frozen, llr, weights, fp32: bool = False, trace: bool = False):
     return (out, tl, tr) if trace else out
 
 
-def wms_backward(frozen, llr, weights, dout):
-    """(dweights [T, m, N/2], dllr [N]) of sum(dout * out) through wms_forward (FP64)."""
+def wms_backward(frozen, llr, weights, dout, fp32: bool = False):
+    """(dweights [T, m, N/2], dllr [N]) of sum(dout * out) through wms_forward: FP64, or with
+    fp32 the binary32 forward and every adjoint operation rounded to binary32."""
     frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
     llr = np.ascontiguousarray(llr, dtype=np.float32)
     w = np.ascontiguousarray(weights, dtype=np.float64)
@@ -332,6 +333,7 @@ def wms_backward(frozen, llr, weights, dout):
     dw = np.zeros_like(w)
     dl = np.zeros(N, np.float64)
     _check(_load().orc_wms_backward(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), w.shape[0],
-                                    _p(w, ctypes.c_double), _p(d, ctypes.c_double), _p(dw, ctypes.c_double),
+                                    _p(w, ctypes.c_double), _p(d, ctypes.c_double), 1 if fp32 else 0,
+                                    _p(dw, ctypes.c_double),
                                     _p(dl, ctypes.c_double)), "wms_backward")
     return dw, dl

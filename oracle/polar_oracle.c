@@ -869,6 +869,8 @@ int orc_max_threads(void)
 /*   input: no adjoint flows into or out of them and they add nothing to a    */
 /*   weight's gradient.                                                       */
 /* ------------------------------------------------------------------------ */
+static double r32(int fp32, double v) { return fp32 ? (double)(float)v : v; }
+
 static double wms_f(int fp32, double w, double x, double y)
 {
     double v = w * sgn(x) * sgn(y) * fmin(fabs(x), fabs(y));
@@ -969,20 +971,27 @@ static void wms_df(double w, double x, double y, double* dx, double* dy)
     }
 }
 
-/* accumulate into an adjoint slot unless the message it belongs to is +-inf */
-static void wms_acc(double* slot, double value, double g)
+/* accumulate into an adjoint slot unless the message it belongs to is +-inf;
+   with fp32 the sum is rounded to binary32, like every other operation */
+static void wms_acc(int fp32, double* slot, double value, double g)
 {
-    if (!isinf(value)) *slot += g;
+    if (!isinf(value)) *slot = r32(fp32, *slot + g);
 }
 
 /*
- * orc_wms_backward -- gradient of a loss through orc_wms_forward (FP64).
+ * orc_wms_backward -- gradient of a loss through orc_wms_forward.
  *   dout   N values dLoss/d out[i]
+ *   fp32   0: FP64 throughout.  1: the forward of orc_wms_forward's fp32 mode,
+ *          and every product and sum of the adjoint rounded to binary32 (the
+ *          weights and dout are taken as binary32 values).  The adjoint is the
+ *          same chain rule in the same order either way: stages m-1 .. 0 of
+ *          iterations T .. 1, PEs in increasing a, and within a PE the outputs
+ *          R[s+1][b], L[s][b], R[s+1][a], L[s][a], then g and t.
  *   dw     T*m*(N/2) gradient of the weights (overwritten)
  *   dllr   N gradient of the channel LLRs (overwritten)
  */
 int orc_wms_backward(int N, const uint8_t* frozen, const float* llr, int T, const double* w, const double* dout,
-                     double* dw, double* dllr)
+                     int fp32, double* dw, double* dllr)
 {
     const int m = ilog2_exact(N);
     if (m < 1 || T < 1 || !frozen || !llr || !w || !dout || !dw || !dllr) return ORC_ERR_ARG;
@@ -993,7 +1002,7 @@ int orc_wms_backward(int N, const uint8_t* frozen, const float* llr, int T, cons
     double* dLp = (double*)calloc(P, sizeof(double)); /* adjoint of the L state before it */
     double* dR = (double*)calloc(P, sizeof(double));
     int rc = (pl && pr && dL && dLp && dR) ? ORC_OK : ORC_ERR_NOMEM;
-    if (rc == ORC_OK) rc = wms_run(N, m, frozen, llr, T, w, 0, pl, pr);
+    if (rc == ORC_OK) rc = wms_run(N, m, frozen, llr, T, w, fp32, pl, pr);
     if (rc == ORC_OK) {
         for (size_t k = 0; k < (size_t)T * (size_t)m * (size_t)(N / 2); ++k) dw[k] = 0.0;
         for (int i = 0; i < N; ++i) dllr[i] = 0.0;
@@ -1005,7 +1014,7 @@ int orc_wms_backward(int N, const uint8_t* frozen, const float* llr, int T, cons
             const double* Rc = pr + (size_t)t * P;       /* R^t */
             for (size_t k = 0; k < P; ++k) dR[k] = 0.0, dLp[k] = 0.0;
             if (t == T)
-                for (int i = 0; i < N; ++i) wms_acc(&dR[(size_t)m * N + i], Rc[(size_t)m * N + i], dout[i]);
+                for (int i = 0; i < N; ++i) wms_acc(fp32, &dR[(size_t)m * N + i], Rc[(size_t)m * N + i], r32(fp32, dout[i]));
             /* the L state of columns m (prior) and 0 (read by nothing) carries no adjoint */
             for (int s = m - 1; s >= 0; --s) {
                 const int h = 1 << (m - 1 - s);
@@ -1013,11 +1022,11 @@ int orc_wms_backward(int N, const uint8_t* frozen, const float* llr, int T, cons
                     if (a & h) continue;
                     const int b = a + h;
                     const size_t widx = ((size_t)(t - 1) * m + s) * (N / 2) + wms_pair_index(m, s, a);
-                    const double wt = w[widx];
+                    const double wt = r32(fp32, w[widx]);
                     const double La = Lp[(size_t)(s + 1) * N + a], Lb = Lp[(size_t)(s + 1) * N + b];
                     const double Ra = Rc[(size_t)s * N + a], Rb = Rc[(size_t)s * N + b];
-                    const double tt = Lb + Rb;
-                    const double g = wt * sgn(La) * sgn(Ra) * fmin(fabs(La), fabs(Ra));
+                    const double tt = r32(fp32, Lb + Rb);
+                    const double g = wms_f(fp32, wt, La, Ra);
                     /* adjoints of the four outputs (zero for +-inf outputs) */
                     const double oLa = Lc[(size_t)s * N + a], oLb = Lc[(size_t)s * N + b];
                     const double oRa = Rc[(size_t)(s + 1) * N + a], oRb = Rc[(size_t)(s + 1) * N + b];
@@ -1027,39 +1036,39 @@ int orc_wms_backward(int N, const uint8_t* frozen, const float* llr, int T, cons
                     const double gRb = isinf(oRb) ? 0.0 : dR[(size_t)(s + 1) * N + b];
                     double dg = 0.0, dt = 0.0, dx, dy;
                     /* R[s+1][b] = Rb + g ; L[s][b] = Lb + g */
-                    wms_acc(&dR[(size_t)s * N + b], Rb, gRb);
-                    if (!isinf(g)) dg += gRb;
-                    wms_acc(&dLp[(size_t)(s + 1) * N + b], Lb, gLb);
-                    if (!isinf(oLb)) dg += gLb;
+                    wms_acc(fp32, &dR[(size_t)s * N + b], Rb, gRb);
+                    if (!isinf(g)) dg = r32(fp32, dg + gRb);
+                    wms_acc(fp32, &dLp[(size_t)(s + 1) * N + b], Lb, gLb);
+                    if (!isinf(oLb)) dg = r32(fp32, dg + gLb);
                     /* R[s+1][a] = f(Ra, t) */
                     if (!isinf(oRa) && gRa != 0.0) {
                         wms_df(wt, Ra, tt, &dx, &dy);
-                        wms_acc(&dR[(size_t)s * N + a], Ra, gRa * dx);
-                        if (!isinf(tt)) dt += gRa * dy;
-                        dw[widx] += gRa * sgn(Ra) * sgn(tt) * fmin(fabs(Ra), fabs(tt));
+                        wms_acc(fp32, &dR[(size_t)s * N + a], Ra, r32(fp32, gRa * dx));
+                        if (!isinf(tt)) dt = r32(fp32, dt + r32(fp32, gRa * dy));
+                        dw[widx] = r32(fp32, dw[widx] + r32(fp32, gRa * (sgn(Ra) * sgn(tt) * fmin(fabs(Ra), fabs(tt)))));
                     }
                     /* L[s][a] = f(La, t) */
                     if (!isinf(oLa) && gLa != 0.0) {
                         wms_df(wt, La, tt, &dx, &dy);
-                        wms_acc(&dLp[(size_t)(s + 1) * N + a], La, gLa * dx);
-                        if (!isinf(tt)) dt += gLa * dy;
-                        dw[widx] += gLa * sgn(La) * sgn(tt) * fmin(fabs(La), fabs(tt));
+                        wms_acc(fp32, &dLp[(size_t)(s + 1) * N + a], La, r32(fp32, gLa * dx));
+                        if (!isinf(tt)) dt = r32(fp32, dt + r32(fp32, gLa * dy));
+                        dw[widx] = r32(fp32, dw[widx] + r32(fp32, gLa * (sgn(La) * sgn(tt) * fmin(fabs(La), fabs(tt)))));
                     }
                     /* g = f(La, Ra) */
                     if (!isinf(g) && dg != 0.0) {
                         wms_df(wt, La, Ra, &dx, &dy);
-                        wms_acc(&dLp[(size_t)(s + 1) * N + a], La, dg * dx);
-                        wms_acc(&dR[(size_t)s * N + a], Ra, dg * dy);
-                        dw[widx] += dg * sgn(La) * sgn(Ra) * fmin(fabs(La), fabs(Ra));
+                        wms_acc(fp32, &dLp[(size_t)(s + 1) * N + a], La, r32(fp32, dg * dx));
+                        wms_acc(fp32, &dR[(size_t)s * N + a], Ra, r32(fp32, dg * dy));
+                        dw[widx] = r32(fp32, dw[widx] + r32(fp32, dg * (sgn(La) * sgn(Ra) * fmin(fabs(La), fabs(Ra)))));
                     }
                     /* t = Lb + Rb */
                     if (!isinf(tt)) {
-                        wms_acc(&dLp[(size_t)(s + 1) * N + b], Lb, dt);
-                        wms_acc(&dR[(size_t)s * N + b], Rb, dt);
+                        wms_acc(fp32, &dLp[(size_t)(s + 1) * N + b], Lb, dt);
+                        wms_acc(fp32, &dR[(size_t)s * N + b], Rb, dt);
                     }
                 }
             }
-            for (int i = 0; i < N; ++i) dllr[i] += dR[i];
+            for (int i = 0; i < N; ++i) dllr[i] = r32(fp32, dllr[i] + dR[i]);
             /* the L state before iteration t: columns 1..m-1 carry over; iteration 1 reads the start state */
             double* tmp = dL;
             dL = dLp;

@@ -224,9 +224,10 @@ HostLayout host_layout(int N, int batch)
     return h;
 }
 
-int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale, int stop_mode,
-                int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates, float* trace_L,
-                float* trace_R, int32_t* trace_P, bool trace, void* stream)
+// The decode parameters that do not depend on the buffers.  The host entry
+// points check them before they enqueue any copy, so that an argument error
+// never leaves a copy from the caller's host buffer in flight.
+int decode_params_check(const polarbp_code* c, int batch, int max_iter, float scale, int stop_mode, int freeze_mode)
 {
     if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
     if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
@@ -239,10 +240,21 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
         return fail(POLARBP_ERR_ARG, "unknown freeze_mode");
     if (freeze_mode == POLARBP_FREEZE_CSFG_MULTI && c->m > 12)
         return fail(POLARBP_ERR_UNSUPPORTED, "POLARBP_FREEZE_CSFG_MULTI supports N <= 4096");
+    if (c->m > 15) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 32768");
+    return POLARBP_OK;
+}
+
+int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter, float scale, int stop_mode,
+                int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates, float* trace_L,
+                float* trace_R, int32_t* trace_P, bool trace, void* stream)
+{
+    {
+        const int rc = decode_params_check(c, batch, max_iter, scale, stop_mode, freeze_mode);
+        if (rc != POLARBP_OK) return rc;
+    }
     if (batch == 0) return POLARBP_OK;
     if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be device pointers");
     if (trace && (!trace_L || !trace_R || !trace_P)) return fail(POLARBP_ERR_ARG, "trace buffers must be given");
-    if (c->m > 15) return fail(POLARBP_ERR_UNSUPPORTED, "decode supports N <= 32768");
     int rc = check_device(c);
     if (rc != POLARBP_OK) return rc;
 
@@ -536,12 +548,18 @@ int polarbp_decode_host(const polarbp_code* c, const float* llr, int batch, int 
                         int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations, int64_t* pe_updates,
                         void* workspace, size_t workspace_bytes, void* stream)
 {
-    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
-    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    {
+        const int rc = decode_params_check(c, batch, max_iter, scale, stop_mode, freeze_mode);
+        if (rc != POLARBP_OK) return rc;
+    }
     if (batch == 0) return POLARBP_OK;
     if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be host pointers");
     const HostLayout h = host_layout(c->N, batch);
     if (!workspace || workspace_bytes < h.total) return fail(POLARBP_ERR_ARG, "workspace too small");
+    {
+        const int rc = check_device(c);
+        if (rc != POLARBP_OK) return rc;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
     float* d_llr = reinterpret_cast<float*>(ws + h.llr);
@@ -558,9 +576,16 @@ int polarbp_decode_host(const polarbp_code* c, const float* llr, int batch, int 
     const bool piped = batch >= 2 * cb;
     std::unique_lock<std::mutex> lock(c->pipe_lock, std::defer_lock);
     cudaError_t e = cudaSuccess;
+    // Once a copy is enqueued, every error return first waits for the streams
+    // used so far, so that no copy from or to the caller's host buffers is left
+    // in flight when the call returns.
+    auto drain = [&](int rc) {
+        if (piped)
+            for (int i = 0; i < kPipe; ++i) cudaStreamSynchronize(c->pipe[i]);
+        cudaStreamSynchronize(s);
+        return rc;
+    };
     if (piped) {
-        int rc = check_device(c);
-        if (rc != POLARBP_OK) return rc;
         lock.lock();
         e = cudaEventRecord(c->pipe_start, s);
         for (int i = 0; i < kPipe && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->pipe[i], c->pipe_start, 0);
@@ -571,24 +596,24 @@ int polarbp_decode_host(const polarbp_code* c, const float* llr, int batch, int 
         cudaStream_t st = piped ? c->pipe[k % kPipe] : s;
         const size_t o = (size_t)off * N, n = (size_t)nb * N;
         e = cudaMemcpyAsync(d_llr + o, llr + o, n * sizeof(float), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "llr upload");
+        if (e != cudaSuccess) return drain(cuda_fail(e, "llr upload"));
         int rc = decode_impl(c, d_llr + o, nb, max_iter, scale, stop_mode, freeze_mode, d_u + o, d_it + off, d_pe + off,
                              nullptr, nullptr, nullptr, false, st);
-        if (rc != POLARBP_OK) return rc;
+        if (rc != POLARBP_OK) return drain(rc);
         e = cudaMemcpyAsync(u_hat + o, d_u + o, n, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && iterations)
             e = cudaMemcpyAsync(iterations + off, d_it + off, (size_t)nb * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && pe_updates)
             e = cudaMemcpyAsync(pe_updates + off, d_pe + off, (size_t)nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_fail(e, "decode_host copies");
+        if (e != cudaSuccess) return drain(cuda_fail(e, "decode_host copies"));
     }
     if (piped) {
         for (int i = 0; i < kPipe && e == cudaSuccess; ++i) {
             e = cudaEventRecord(c->pipe_done[i], c->pipe[i]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->pipe_done[i], 0);
         }
+        if (e != cudaSuccess) return drain(cuda_fail(e, "decode_host pipeline"));
         lock.unlock();
-        if (e != cudaSuccess) return cuda_fail(e, "decode_host pipeline");
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "decode_host copies");
@@ -621,9 +646,16 @@ int polarbp_decode_host_noalloc(const polarbp_code* c, const float* llr, int bat
                                 int stop_mode, int freeze_mode, uint8_t* u_hat, int32_t* iterations,
                                 int64_t* pe_updates, void* stream)
 {
-    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
-    if (batch < 0) return fail(POLARBP_ERR_ARG, "batch must be >= 0");
+    {
+        const int rc = decode_params_check(c, batch, max_iter, scale, stop_mode, freeze_mode);
+        if (rc != POLARBP_OK) return rc;
+    }
     if (batch == 0) return POLARBP_OK;
+    {
+        // the scratch address below is looked up on the current device: it must be the handle's
+        const int rc = check_device(c);
+        if (rc != POLARBP_OK) return rc;
+    }
     const size_t need = host_layout(c->N, batch).total;
     if (need > POLARBP_NOALLOC_SCRATCH_BYTES) {
         size_t fit = 0;

@@ -104,9 +104,12 @@ __global__ void wms_forward_kernel(const float* __restrict__ llr, const uint32_t
     for (int i = threadIdx.x; i < N; i += blockDim.x) out[cw * N + i] = __fadd_rn(R[m * N + i], L[m * N + i]);
 }
 
+// Every product and sum of the adjoint is rounded on its own (no fused
+// multiply-add): the adjoint is binary32 arithmetic operation by operation, in
+// the chain-rule order written below.
 __device__ __forceinline__ void acc(float* slot, float value, float g)
 {
-    if (!isinf(value)) *slot += g;
+    if (!isinf(value)) *slot = __fadd_rn(*slot, g);
 }
 
 // partials: [batch][T m N/2]
@@ -168,23 +171,23 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
                 const float gRb = isinf(oRb) ? 0.f : dR[(s + 1) * N + b];
                 float dg = 0.f, dt = 0.f, dw = 0.f;
                 acc(&dR[s * N + b], Rb, gRb);
-                if (!isinf(g)) dg += gRb;
+                if (!isinf(g)) dg = __fadd_rn(dg, gRb);
                 acc(&dLp[(s + 1) * N + b], Lb, gLb);
-                if (!isinf(oLb)) dg += gLb;
+                if (!isinf(oLb)) dg = __fadd_rn(dg, gLb);
                 if (!isinf(oRa) && gRa != 0.f) {
-                    if (fabsf(Ra) <= fabsf(tt)) acc(&dR[s * N + a], Ra, gRa * wt * wsgn(tt));
-                    else if (!isinf(tt)) dt += gRa * wt * wsgn(Ra);
-                    dw += gRa * hval(Ra, tt);
+                    if (fabsf(Ra) <= fabsf(tt)) acc(&dR[s * N + a], Ra, __fmul_rn(__fmul_rn(gRa, wt), wsgn(tt)));
+                    else if (!isinf(tt)) dt = __fadd_rn(dt, __fmul_rn(__fmul_rn(gRa, wt), wsgn(Ra)));
+                    dw = __fadd_rn(dw, __fmul_rn(gRa, hval(Ra, tt)));
                 }
                 if (!isinf(oLa) && gLa != 0.f) {
-                    if (fabsf(La) <= fabsf(tt)) acc(&dLp[(s + 1) * N + a], La, gLa * wt * wsgn(tt));
-                    else if (!isinf(tt)) dt += gLa * wt * wsgn(La);
-                    dw += gLa * hval(La, tt);
+                    if (fabsf(La) <= fabsf(tt)) acc(&dLp[(s + 1) * N + a], La, __fmul_rn(__fmul_rn(gLa, wt), wsgn(tt)));
+                    else if (!isinf(tt)) dt = __fadd_rn(dt, __fmul_rn(__fmul_rn(gLa, wt), wsgn(La)));
+                    dw = __fadd_rn(dw, __fmul_rn(gLa, hval(La, tt)));
                 }
                 if (!isinf(g) && dg != 0.f) {
-                    if (fabsf(La) <= fabsf(Ra)) acc(&dLp[(s + 1) * N + a], La, dg * wt * wsgn(Ra));
-                    else acc(&dR[s * N + a], Ra, dg * wt * wsgn(La));
-                    dw += dg * hval(La, Ra);
+                    if (fabsf(La) <= fabsf(Ra)) acc(&dLp[(s + 1) * N + a], La, __fmul_rn(__fmul_rn(dg, wt), wsgn(Ra)));
+                    else acc(&dR[s * N + a], Ra, __fmul_rn(__fmul_rn(dg, wt), wsgn(La)));
+                    dw = __fadd_rn(dw, __fmul_rn(dg, hval(La, Ra)));
                 }
                 if (!isinf(tt)) {
                     acc(&dLp[(s + 1) * N + b], Lb, dt);
@@ -196,7 +199,7 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
         }
         for (int j = 0; j < 4; ++j) {
             const int i = threadIdx.x + j * blockDim.x;
-            if (i < N) dl_acc[j] += dR[i];
+            if (i < N) dl_acc[j] = __fadd_rn(dl_acc[j], dR[i]);
         }
         __syncthreads();
         float* tmp = dL;
@@ -229,7 +232,7 @@ __global__ void wms_reduce_chunks_kernel(const float* __restrict__ partial, int 
     const int c0 = q * kReduceChunk, c1 = min(batch, c0 + kReduceChunk);
     float acc_v = 0.f;
 #pragma unroll 8
-    for (int c = c0; c < c1; ++c) acc_v += partial[(size_t)c * W + k];
+    for (int c = c0; c < c1; ++c) acc_v = __fadd_rn(acc_v, partial[(size_t)c * W + k]);
     chunk[(size_t)q * W + k] = acc_v;
 }
 
@@ -238,7 +241,7 @@ __global__ void wms_reduce_kernel(const float* __restrict__ chunk, int nchunks, 
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= W) return;
     float acc_v = 0.f;
-    for (int q = 0; q < nchunks; ++q) acc_v += chunk[(size_t)q * W + k];
+    for (int q = 0; q < nchunks; ++q) acc_v = __fadd_rn(acc_v, chunk[(size_t)q * W + k]);
     dw[k] = acc_v;
 }
 

@@ -47,7 +47,8 @@ def test_library_is_built_for_sm_103a(lib):
 
 @pytest.mark.parametrize("N,K", [(2, 1), (8, 4), (64, 32), (128, 64), (256, 64), (256, 128), (256, 192),
                                  (1024, 256), (1024, 512), (1024, 768), (4096, 1024), (4096, 2048),
-                                 (4096, 3072), (8192, 4096), (16384, 8192), (32768, 16384), (16, 0), (16, 16)])
+                                 (4096, 3072), (8192, 4096), (16384, 8192), (32768, 16384), (16, 0), (16, 16),
+                                 (64, 1), (1024, 1023), (8192, 0), (8192, 1), (8192, 8191), (8192, 8192)])
 def test_frozen_set_matches_oracle(lib, N, K):
     """Sec. II construction: the library's host recursion and the oracle agree exactly."""
     assert np.array_equal(B.polarbp_frozen_set(N, K, 0.5), O.bec_frozen(N, K, 0.5))

@@ -119,7 +119,7 @@ def test_cluster_noiseless_invariants(B, N):
     K = N // 2
     M = N.bit_length() - 1
     code = B.polarbp_construct(N, K)
-    fz = code.frozen_mask()
+    fz = O.bec_frozen(N, K)
     u = I.info_bits(3, np.arange(3), fz)
     llr = I.noiseless_llr(O.encode(u), 3.0)
     for mode, iters, pe in (((1, 0), 1, M * N // 2), ((0, 1), 2, 3 * N // 2 - 1), ((1, 1), 1, N - 1),
@@ -134,7 +134,7 @@ def test_cluster_noiseless_invariants(B, N):
 def test_cluster_degenerate_rates(B, K, mode):
     N = 8192
     code = B.polarbp_construct(N, K)
-    fz = code.frozen_mask()
+    fz = O.bec_frozen(N, K)
     rng = np.random.default_rng(K)
     llr = rng.normal(1.0, 2.0, (4, N)).astype(np.float32)
     uh, it, pe = gpu_decode(B, code, llr, 20, *mode)
@@ -154,7 +154,7 @@ def test_cluster_device_generator_and_full_batch_sampled(B):
     uh, it, pe = uh.cpu().numpy(), it.cpu().numpy(), pe.cpu().numpy()
     sample = np.array([0, 1, 777, 1024, 2047])
     hllr = llr.cpu().numpy()[sample]
-    fz = code.frozen_mask()
+    fz = O.bec_frozen(N, K)
     ouh, oit, ope, _ = O.decode_batch(fz, hllr, 100, ALPHA, 1, 1, fp32=True)
     assert np.array_equal(uh[sample], ouh) and np.array_equal(it[sample], oit) and np.array_equal(pe[sample], ope)
     assert np.all((it >= 1) & (it <= 100))

@@ -214,7 +214,7 @@ def test_noiseless_invariants(B, N):
     K = N // 2
     M = N.bit_length() - 1
     code = B.polarbp_construct(N, K)
-    fz = code.frozen_mask()
+    fz = O.bec_frozen(N, K)
     u = I.info_bits(3, np.arange(5), fz)
     llr = I.noiseless_llr(O.encode(u), 3.0)
     for mode, iters, pe in (((1, 0), 1, M * N // 2), ((0, 1), 2, 3 * N // 2 - 1), ((1, 1), 1, N - 1),
@@ -228,7 +228,7 @@ def test_noiseless_invariants(B, N):
 @pytest.mark.parametrize("mode", MODES)
 def test_degenerate_rates(B, N, K, mode):
     code = B.polarbp_construct(N, K)
-    fz = code.frozen_mask()
+    fz = O.bec_frozen(N, K)
     rng = np.random.default_rng(K)
     llr = rng.normal(1.0, 2.0, (20, N)).astype(np.float32)
     uh, it, pe = gpu_decode(B, code, llr, 20, *mode)

@@ -95,7 +95,7 @@ def test_decisions_match_oracle(B, N, stop):
 def test_noiseless_stops_at_iteration_m(B, N):
     m = N.bit_length() - 1
     code = B.polarbp_construct(N, N // 2)
-    fz = code.frozen_mask()
+    fz = O.bec_frozen(N, N // 2)
     u = I.info_bits(12, np.arange(16), fz)
     llr = I.noiseless_llr(O.encode(u), 2.5)
     uh, it, pe = gpu_flood(B, code, llr, 3 * m, 1)

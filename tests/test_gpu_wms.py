@@ -68,8 +68,39 @@ def test_constant_weights_match_the_decoder(B):
     assert torch.equal(ck[:, :, 0], tL) and torch.equal(ck[:, :, 1], tR)
 
 
+def branch_signature(fz, llr, w, fp32):
+    """Every comparison and sign the adjoint of Eq. (1) branches on, for all PEs of all
+    iterations of one codeword: |Ra| <= |t|, |La| <= |t|, |La| <= |Ra| and the signs of
+    La, Ra and t = Lb + Rb, from the oracle's forward planes."""
+    N = fz.shape[0]
+    m = N.bit_length() - 1
+    _, tl, tr = O.wms_forward(fz, llr, w.astype(np.float64), fp32=fp32, trace=True)
+    prior = np.zeros((m + 1, N))
+    prior[m] = np.where(fz == 1, np.inf, 0.0)
+    sig = []
+    for t in range(tl.shape[0]):
+        Lp = prior if t == 0 else tl[t - 1]
+        for s in range(m):
+            h = 1 << (m - 1 - s)
+            a = np.array([i for i in range(N) if not i & h])
+            La, Lb, Ra, Rb = Lp[s + 1][a], Lp[s + 1][a + h], tr[t][s][a], tr[t][s][a + h]
+            with np.errstate(invalid="ignore"):
+                tt = Lb + Rb
+            sig += [np.abs(Ra) <= np.abs(tt), np.abs(La) <= np.abs(tt), np.abs(La) <= np.abs(Ra),
+                    np.sign(La), np.sign(Ra), np.sign(tt)]
+    return np.concatenate([np.asarray(x, np.float64).ravel() for x in sig])
+
+
 @pytest.mark.parametrize("N,T", [(16, 10), (128, 10), (256, 10)])
-def test_gradient_matches_fp64_oracle(B, N, T):
+def test_gradient_matches_oracle_element_by_element(B, N, T):
+    """The adjoint of Eq. (1) with per-PE weights, entry by entry.
+    * Against the oracle's binary32 adjoint (every operation rounded to binary32, the same
+      chain-rule order): the LLR gradient of every codeword and the weight gradient, summed
+      over the batch in codeword order, are bit-exact.
+    * Against the FP64 adjoint: on codewords whose binary32 forward takes every min and sign
+      branch the FP64 forward takes, every entry is within 1e-4 relative or 1e-5 absolute.
+      The others are flagged and counted; their dout is zeroed in a second backward pass so
+      that the batch-summed weight gradient is compared over the unflagged codewords alone."""
     batch = 12
     fz, u, llr, w = inputs(N, T, batch, 40 + N)
     code = B.polarbp_construct(N, N // 2)
@@ -80,18 +111,39 @@ def test_gradient_matches_fp64_oracle(B, N, T):
     d_w = torch.from_numpy(w).cuda()
     ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
     B.polarbp_wms_forward(code, d_llr, d_w, ws)
-    gw, gl = B.polarbp_wms_backward(code, d_llr, d_w, torch.from_numpy(dout).cuda(), ws)
-    torch.cuda.synchronize()
-    gw, gl = gw.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64)
-    ow = np.zeros_like(w, dtype=np.float64)
-    ol = np.zeros((batch, N))
+
+    def gpu_backward(d):
+        gw, gl = B.polarbp_wms_backward(code, d_llr, d_w, torch.from_numpy(d).cuda(), ws)
+        torch.cuda.synchronize()
+        return gw.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64)
+
+    gw, gl = gpu_backward(dout)
+    w64 = w.astype(np.float64)
+    ow32 = np.zeros(w.shape, np.float32)
     for c in range(batch):
-        dw_c, dl_c = O.wms_backward(fz, llr[c], w.astype(np.float64), dout[c].astype(np.float64))
+        dw_c, dl_c = O.wms_backward(fz, llr[c], w64, dout[c].astype(np.float64), fp32=True)
+        assert np.array_equal(gl[c], dl_c), c
+        ow32 = (ow32 + dw_c.astype(np.float32)).astype(np.float32)
+    assert np.array_equal(gw, ow32.astype(np.float64))
+
+    flagged = [c for c in range(batch)
+               if not np.array_equal(branch_signature(fz, llr[c], w, True), branch_signature(fz, llr[c], w, False))]
+    print(f"N={N}: {len(flagged)} of {batch} codewords take a different branch in binary32")
+    assert len(flagged) <= batch // 2
+    d2 = dout.copy()
+    d2[flagged] = 0.0
+    gw2, gl2 = gpu_backward(d2)
+    ow = np.zeros_like(w64)
+    for c in range(batch):
+        if c in flagged:
+            continue
+        dw_c, dl_c = O.wms_backward(fz, llr[c], w64, d2[c].astype(np.float64))
         ow += dw_c
-        ol[c] = dl_c
-    for g, o in ((gw, ow), (gl, ol)):
-        assert np.linalg.norm(g - o) <= 1e-4 * np.linalg.norm(o) + 1e-6
-        assert np.mean(np.abs(g - o) <= 1e-4 * np.abs(o).max() + 1e-6) >= 0.999
+        err = np.abs(gl2[c] - dl_c)
+        assert np.all((err <= 1e-4 * np.abs(dl_c)) | (err <= 1e-5)), (c, err.max())
+    err = np.abs(gw2 - ow)
+    bad = ~((err <= 1e-4 * np.abs(ow)) | (err <= 1e-5))
+    assert not bad.any(), (int(bad.sum()), float(err[bad].max()))
 
 
 def test_autograd_function_and_training_step(B):

@@ -77,3 +77,39 @@ def test_gradient_matches_central_differences(N, T, seed):
         fm = F(w, lm.astype(np.float32))
         fd = (fp - fm) / (float(np.float32(lp[i])) - float(np.float32(lm[i])))
         assert abs(fd - dl[i]) <= 1e-4 * max(1.0, abs(dl[i])), (i, fd, dl[i])
+
+
+@pytest.mark.parametrize("N,T,seed", [(16, 3, 11), (32, 4, 12)])
+def test_binary32_adjoint_equals_fp64_when_nothing_rounds(N, T, seed):
+    """The binary32 mode of the adjoint applies the same chain rule as the FP64 one: with
+    LLRs on a grid of 1/8, weights in {1/2, 3/4, 1} and integer dout, every forward and
+    adjoint value has few significant bits, nothing rounds, and the two modes agree exactly
+    (a term dropped or reordered in one mode alone would break this)."""
+    m = N.bit_length() - 1
+    fz = O.bec_frozen(N, N // 2)
+    rng = np.random.default_rng(seed)
+    llr = (rng.integers(-40, 41, N) / 8.0).astype(np.float32)
+    w = rng.choice([0.5, 0.75, 1.0], (T, m, N // 2))
+    dout = rng.integers(-3, 4, N).astype(np.float64)
+    dout[fz == 1] = 0.0
+    dw64, dl64 = O.wms_backward(fz, llr, w, dout)
+    dw32, dl32 = O.wms_backward(fz, llr, w, dout, fp32=True)
+    assert np.array_equal(dw32, dw64) and np.array_equal(dl32, dl64)
+    assert np.count_nonzero(dw64) > 10
+    # every value is a binary32 number
+    assert np.array_equal(dw32.astype(np.float32).astype(np.float64), dw32)
+
+
+def test_binary32_adjoint_close_to_fp64():
+    """On channel inputs the binary32 adjoint differs from FP64 only by rounding."""
+    N, T = 64, 10
+    fz, llr, w = setup(N, T, 21)
+    dout = np.random.default_rng(22).normal(0, 1, N)
+    dout[fz == 1] = 0.0
+    dout = dout.astype(np.float32).astype(np.float64)
+    w = w.astype(np.float32).astype(np.float64)
+    dw64, dl64 = O.wms_backward(fz, llr, w, dout)
+    dw32, dl32 = O.wms_backward(fz, llr, w, dout, fp32=True)
+    for a, b in ((dw32, dw64), (dl32, dl64)):
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+    assert np.array_equal(dw32.astype(np.float32).astype(np.float64), dw32)

@@ -65,13 +65,32 @@ def test_two_calls_match_the_workspace_entry_point(B, N, K, batch):
         assert not np.array_equal(got[0][0], got[1][0])
 
 
-def test_oversized_batch_is_rejected(B):
-    code = B.polarbp_construct(1024, 512)
-    batch = 4000  # 4000 x (4 KiB + 1 KiB + 12 B) > 16 MiB
-    h = _pinned((batch, 1024), torch.float32)
+@pytest.mark.parametrize("N,K", [(1024, 512), (32768, 16384)])
+def test_limit_is_exact(B, N, K):
+    """A batch one codeword over the limit is rejected with the limit in the message; a batch
+    of exactly the limit fits and decodes as polarbp_decode_host does with a workspace."""
+    import re
+    code = B.polarbp_construct(N, K)
+    over = (16 << 20) // (N * 5) + 8  # 4 B of LLR + 1 B of u_hat per position: surely too many
+    h = _pinned((over, N), torch.float32)
     h.zero_()
-    u, it, pe = _pinned((batch, 1024), torch.uint8), _pinned(batch, torch.int32), _pinned(batch, torch.int64)
+    u, it, pe = _pinned((over, N), torch.uint8), _pinned(over, torch.int32), _pinned(over, torch.int64)
     with pytest.raises(B.PolarBPError) as e:
         B.polarbp_decode_host_noalloc(code, h, 10, 0.9375, 1, 1, u, it, pe)
     assert e.value.code == B.POLARBP_ERR_ARG
-    assert "at most" in str(e.value) and "16 MiB" in str(e.value)
+    assert "16 MiB" in str(e.value)
+    limit = int(re.search(r"at most (\d+) codewords", str(e.value)).group(1))
+    assert 0 < limit < over
+    assert B.polarbp_decode_host_workspace(code, limit) <= 16 << 20 < B.polarbp_decode_host_workspace(code, limit + 1)
+    with pytest.raises(B.PolarBPError) as e:
+        B.polarbp_decode_host_noalloc(code, h[: limit + 1], 10, 0.9375, 1, 1, u[: limit + 1], it[: limit + 1],
+                                      pe[: limit + 1])
+    assert e.value.code == B.POLARBP_ERR_ARG
+    _, llr = B.polarbp_awgn(code, 21, 0, limit, 3.0, with_u=False)
+    hl = _pinned((limit, N), torch.float32)
+    hl.copy_(llr)
+    torch.cuda.synchronize()
+    want = _with_workspace(B, code, hl, 20, (1, 1))
+    got = _no_alloc(B, code, hl, 20, (1, 1))
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
