@@ -729,6 +729,140 @@ __device__ __forceinline__ bool gmatrix_ok(Smem<M>& sm, int P, int lane)
     return __all_sync(kFull, same);
 }
 
+// Stages 1..M in order under reading A for codes of N >= 256 (natural-order
+// snapshot rows); the same freezes, stored bits, feedback events and PE count as
+// resolve<M, false>, with less serial work.
+//  * Stages 1..M-6 (CSFGs of >= 64 positions) are checked speculatively at the
+//    frontier as in resolve.  They rarely pass, so this is usually one round.
+//  * Stages M-5..M (CSFGs of <= 32 positions).  With the frontier P at the end of
+//    the large stages, every CSFG these stages can check lies in the two words
+//    w0 = P / 32 and w0 + 1: the stage-(M-5) CSFG is word w0 itself, and the
+//    freezes of the deeper stages add up to less than 32 positions.  Twelve lanes
+//    evaluate Eqs. (2)-(4) for every aligned CSFG of their stage in one of those
+//    words at once (the transform of Eq. (3) acts on each aligned block of a word
+//    independently, and a fold of the failing bits gives one pass bit per CSFG),
+//    then every lane runs the six-stage chain on the pass bits in registers.
+//  * Only the first freeze of an iteration can complete enclosing CSFGs (it ends
+//    at a multiple of its own size; each later freeze adds a smaller power of
+//    two), so propagate() runs once.
+template <int M>
+__device__ __forceinline__ int resolve_fast(Smem<M>& sm, int& P, int lane)
+{
+    using SP = Spec<M>;
+    constexpr int N = Geo<M>::N, NW = Geo<M>::NW;
+    constexpr int JB = M - 6;  // stages with CSFGs of >= 64 positions
+    constexpr int JS = M - 5;  // first stage with CSFGs of <= 32 positions
+    static_assert(natural_rows<M>() && JB >= 2 && SP::JB == JB + 1, "codes of N >= 256");
+    int Ps = P;  // lane s (1 <= s < M): P after the check of stage s
+    bool first = true;
+    int jmin = 1;
+    {
+        SpecSlots<M> ss;
+        spec_slots<M>(ss, lane);
+#pragma unroll 1
+        while (jmin <= JB && P < N) {
+            Spec<M> sp;
+            speculate<M, false>(sm, sp, ss, P, jmin, lane);
+            const unsigned wanted = ((2u << JB) - 1u) & ~((1u << jmin) - 1u);
+            const unsigned pass = ~(unsigned)sp.fail & wanted;
+            if (!pass) break;
+            const int J = __ffs(pass) - 1;
+            const int cand = (P >> (M - J)) << (M - J);
+#pragma unroll
+            for (int r = 0; r < SP::R; ++r) {
+                if (sp.lvl[r] == J) {
+                    sm.U[(cand >> 5) + sp.w[r]] = sp.u[r];
+                    sm.Xf[J * NW + (cand >> 5) + sp.w[r]] = sp.x[r];
+                }
+            }
+            note_event(sm, J, cand, cand + (N >> J), lane);
+            P = cand + (N >> J);
+            __syncwarp();
+            propagate<M>(sm, P, J, lane);
+            if (lane >= J) Ps = P;
+            first = false;
+            jmin = J + 1;
+        }
+    }
+    if (P < N) {
+        const int w0 = P >> 5;
+        // lane l < 12: stage JS + l/2 on word w0 + (l & 1)
+        const int jl = JS + (lane >> 1);
+        const int wl = w0 + (lane & 1);
+        const int Sl = N >> (jl < M ? jl : M);
+        uint32_t x = 0u, u = 0u, pw = 0u;
+        if (lane < 12 && wl < NW) {
+            x = snap_word<M>(sm.hd, jl, 32 * wl);
+            u = x;
+#pragma unroll
+            for (int h = 1; h < 32; h <<= 1)
+                if (h < Sl) u ^= (u >> h) & xmask(h);
+            uint32_t bad = u & sm.Fz[wl];
+#pragma unroll
+            for (int h = 1; h < 32; h <<= 1)
+                if (h < Sl) bad |= bad >> h;
+            // bits at the first position of every aligned block of Sl positions
+            const uint32_t starts = Sl == 1 ? 0xffffffffu : Sl == 2 ? 0x55555555u : Sl == 4 ? 0x11111111u
+                                  : Sl == 8 ? 0x01010101u : Sl == 16 ? 0x00010001u : 0x00000001u;
+            pw = ~bad & starts;
+        }
+        uint32_t pa[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) pa[i] = __shfl_sync(kFull, pw, i);
+        unsigned frz = 0u;  // bit jj: stage JS + jj froze
+        int mybs = 0;       // start of the CSFG frozen at this lane's stage
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) {
+            const int S = N >> (JS + jj);
+            if (P < N) {
+                const int bs = P & ~(S - 1);
+                const int off = bs - 32 * w0;  // 0 <= off < 64
+                const uint32_t word = off < 32 ? pa[2 * jj] : pa[2 * jj + 1];
+                if ((word >> (off & 31)) & 1u) {
+                    frz |= 1u << jj;
+                    if ((lane >> 1) == jj) mybs = bs;
+                    P = bs + S;
+                    if (lane >= JS + jj) Ps = P;
+                }
+            }
+        }
+        if (frz) {
+            // stored bits and feedback decisions of the frozen CSFGs; several can share a
+            // word of U, so U's two words are merged across lanes first
+            uint32_t mk = 0u;
+            if (lane < 12 && ((frz >> (lane >> 1)) & 1u) && (mybs >> 5) == wl)
+                mk = low_mask(Sl) << (mybs & 31);
+            const uint32_t ue = __reduce_or_sync(kFull, (lane & 1) ? 0u : mk);
+            const uint32_t uo = __reduce_or_sync(kFull, (lane & 1) ? mk : 0u);
+            const uint32_t ve = __reduce_or_sync(kFull, (lane & 1) ? 0u : (u & mk));
+            const uint32_t vo = __reduce_or_sync(kFull, (lane & 1) ? (u & mk) : 0u);
+            if (lane < 2 && w0 + lane < NW) {
+                const uint32_t m2 = lane ? uo : ue, v2 = lane ? vo : ve;
+                if (m2) sm.U[w0 + lane] = (sm.U[w0 + lane] & ~m2) | v2;
+            }
+            if (mk) {
+                uint32_t* px = sm.Xf + jl * NW + wl;
+                *px = (*px & ~mk) | (x & mk);
+                if (jl == M) sm.Lm[mybs] = (x >> (mybs & 31)) & 1u ? -INFINITY : INFINITY;
+                else {
+                    sm.ev_lo()[jl] = mybs;
+                    sm.ev_hi()[jl] = mybs + Sl;
+                }
+            }
+            if (lane == 0) sm.ctl[CTL_EVENT] |= (int)((frz << JS) & ~(1u << M));
+            __syncwarp();
+            if (first) {
+                const int jf = JS + __ffs(frz) - 1;
+                const int Sf = N >> jf;
+                const int bf = __shfl_sync(kFull, mybs, 2 * (jf - JS));
+                propagate<M>(sm, bf + Sf, jf, lane);
+            }
+        }
+    }
+    const int pe = (lane >= 1 && lane < M) ? (N - ((Ps >> (M - lane)) << (M - lane))) >> 1 : 0;
+    return (int)__reduce_add_sync(kFull, (unsigned)pe) + (N >> 1);
+}
+
 template <int M, bool GSTOP, bool FREEZE, bool MULTI>
 __device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
 {
@@ -743,7 +877,8 @@ __device__ __forceinline__ void checker(unsigned char* smem_base, int lane)
     int P = sm.ctl[CTL_P];
     int pe_it = N >> 1;  // stage 0 always runs
     if constexpr (FREEZE) {
-        pe_it = resolve<M, MULTI>(sm, P, lane);
+        if constexpr (natural_rows<M>() && !MULTI) pe_it = resolve_fast<M>(sm, P, lane);
+        else pe_it = resolve<M, MULTI>(sm, P, lane);
     } else {
         pe_it = M * (N >> 1);
     }
@@ -899,7 +1034,10 @@ __device__ __forceinline__ void snap_row(uint8_t* row, uint32_t byte, int tid)
 // of M + XC stages (stage s here is stage s + XC there): P0 is then the covered
 // prefix within this part, stage 0 may be covered, its L column is stored, the
 // channel-side decisions are taken elsewhere and trace columns are N << XC apart.
-template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE, int XC = 0>
+// KEEP (default: FREEZE) protects the L outputs of covered PEs with keep-selects;
+// the pipelined decoder (bp_pipe.cuh) keeps covered CSFGs at a fixed point of
+// Eq. (1) instead and runs every PE unguarded.
+template <int M, int PH, int Q, bool GSTOP, bool FREEZE, bool TRACE, int XC = 0, bool KEEP = FREEZE>
 __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int P0, float alpha, const CwIO& a,
                                           long long trace_base)
 {
@@ -910,7 +1048,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
     constexpr int k = b - G::lo(PH);
     constexpr bool snap = FREEZE || (GSTOP && s == M - 1);
     constexpr long long TSTRIDE = (long long)N << XC;
-    const int thr = (s + XC == 0 || !FREEZE) ? 0 : ((P0 >> (M - s)) << (M - s));
+    const int thr = (s + XC == 0 || !KEEP) ? 0 : ((P0 >> (M - s)) << (M - s));
     uint32_t xbyte = 0;  // stage 0: decisions on R[0] + L[0] (G-matrix stop)
     uint32_t xb[8];      // the same as ballots, for rows built from ballots
     // padded bases for the boundary columns read (s+1) and written (s) here
@@ -938,7 +1076,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         const int e2 = e | (1 << k);
         const int ia = elem_index<M, PH>(tid, e);
         const int ib = ia + (1 << b);
-        const bool covered = FREEZE && s + XC > 0 && ia < thr;  // PE inside a covered CSFG
+        const bool covered = KEEP && s + XC > 0 && ia < thr;  // PE inside a covered CSFG
         float La, Lb;
         if constexpr (s + 1 == M) {
             La = lm[e];
@@ -1008,7 +1146,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
             a.trace_R[trace_base + (long long)(s + 1) * TSTRIDE + elem_index<M, PH>(tid, e)] = rg.R[e];
     }
     if constexpr (Q + 1 < G::cnt(PH))
-        run_stage<M, PH, Q + 1, GSTOP, FREEZE, TRACE, XC>(rg, sm, tid, P0, alpha, a, trace_base);
+        run_stage<M, PH, Q + 1, GSTOP, FREEZE, TRACE, XC, KEEP>(rg, sm, tid, P0, alpha, a, trace_base);
 }
 
 template <int M, int PH, bool GSTOP, bool FREEZE, bool TRACE, int CPC, int XC = 0>
@@ -1044,11 +1182,11 @@ __device__ __forceinline__ void run_phase(Regs<M>& rg, Smem<M>& sm, int tid, boo
 // columns in their owner phase's mapping, shared-memory columns in the mapping of
 // the phase that reads them (stage C-1).  No barrier is needed.
 template <int M, int C>
-__device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, int mask)
+__device__ __forceinline__ void apply_column(Regs<M>& rg, Smem<M>& sm, int tid)
 {
     using G = Geo<M>;
-    if constexpr (C <= M) {
-        if (mask & (1 << C)) {
+    {
+        {
             const int lo = sm.ev_lo()[C], hi = sm.ev_hi()[C];
             const uint32_t* xf = sm.Xf + C * G::NW;
             constexpr int PH = G::is_boundary(C) ? (C - 1) / 3 : G::owner(C);
@@ -1091,6 +1229,14 @@ __device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, 
                 }
             }
         }
+    }
+}
+
+template <int M, int C>
+__device__ __forceinline__ void apply_events(Regs<M>& rg, Smem<M>& sm, int tid, int mask)
+{
+    if constexpr (C <= M) {
+        if (mask & (1 << C)) apply_column<M, C>(rg, sm, tid);
         apply_events<M, C + 1>(rg, sm, tid, mask);
     }
 }

@@ -1,5 +1,5 @@
 // Decode kernels for N = 2 .. 256 (instantiations of bp_decode.cuh).
-#include "bp_decode.cuh"
+#include "bp_pipe.cuh"
 
 namespace polarbp {
 cudaError_t launch_m1(const LaunchReq& q) { return launch_decode<1>(q); }
@@ -9,5 +9,5 @@ cudaError_t launch_m4(const LaunchReq& q) { return launch_decode<4>(q); }
 cudaError_t launch_m5(const LaunchReq& q) { return launch_decode<5>(q); }
 cudaError_t launch_m6(const LaunchReq& q) { return launch_decode<6>(q); }
 cudaError_t launch_m7(const LaunchReq& q) { return launch_decode<7>(q); }
-cudaError_t launch_m8(const LaunchReq& q) { return launch_decode<8>(q); }
+cudaError_t launch_m8(const LaunchReq& q) { return launch_decode_pipe<8>(q); }
 }  // namespace polarbp
