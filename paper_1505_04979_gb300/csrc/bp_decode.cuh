@@ -308,13 +308,58 @@ __device__ __forceinline__ int snap_lo(int c)
     return (ph == Geo<M>::NP - 1) ? 0 : (M - 3 - 3 * ph);
 }
 
-// Codes of N >= 256 (every phase has whole warps) store every snapshot row as
-// natural-order words, written by snap_row below; smaller codes keep one byte
-// per thread and gather with hd_word.
+// Codes of N >= 256 (every phase has whole warps) store the snapshot rows of the
+// phases with register bits from bit lo >= 1 as raw ballots (raw_word below) and
+// the last phase's rows (lo = 0) as one byte per thread, which is natural order;
+// smaller codes keep one byte per thread and gather with hd_word.
 template <int M>
 __host__ __device__ constexpr bool natural_rows()
 {
     return M >= 8;
+}
+
+// Decisions of positions [i0, i0 + 32) (i0 a multiple of 32) from a raw ballot
+// row: word 8 k + e holds, in bit l, the decision on element e of thread 32 k + l
+// of a phase whose register bits start at bit lo >= 1, i.e. on position
+// p = (t & (2^lo - 1)) | e << lo | (t >> lo) << (lo + 3), t = 32 k + l.  For
+// lo <= 4 the warp is k = p >> 8.
+__device__ __forceinline__ uint32_t raw_word(const uint32_t* row, int lo, int i0)
+{
+    const int q = i0 >> 5;
+    if (lo >= 5) {
+        // the lanes of a warp hold 32 consecutive positions of each element: one ballot
+        const int k = ((i0 & ((1 << lo) - 1)) >> 5) | ((i0 >> (lo + 3)) << (lo - 5));
+        return row[8 * k + ((i0 >> lo) & 7)];
+    }
+    const uint32_t* r = row + 8 * (i0 >> 8);
+    if (lo == 4) {
+        // positions b < 16 / b >= 16 of the word: elements 2 (q & 3) and + 1, lanes 16 h ..
+        const int e = 2 * (q & 3), h = (q >> 2) & 1;
+        return __byte_perm(r[e], r[e + 1], h ? 0x7632u : 0x5410u);
+    }
+    if (lo == 3) {
+        // elements 4 (q & 1) .. + 3, byte g of each
+        const int e = 4 * (q & 1);
+        const uint32_t g = (q >> 1) & 3, sel = g | ((4u + g) << 4);
+        return __byte_perm(__byte_perm(r[e], r[e + 1], sel), __byte_perm(r[e + 2], r[e + 3], sel), 0x5410u);
+    }
+    // lo = 2, 1: nibble g = q & 7 (lanes 4 g .. 4 g + 3) of each of the 8 elements
+    const int g4 = 4 * (q & 7);
+    uint32_t n[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) n[e] = (r[e] >> g4) & 0xFu;
+    const uint32_t x = n[0] | (n[1] << 4) | (n[2] << 8) | (n[3] << 12) | (n[4] << 16) | (n[5] << 20) |
+                       (n[6] << 24) | (n[7] << 28);  // position bits 0-1: lane bits 0-1, bits 2-4: element
+    if (lo == 2) return x;
+    // lo = 1: lane bit 0 is position bit 0, lane bit 1 position bit 4, the element bits 1-3
+    uint32_t a = x & 0x33333333u, b = (x >> 2) & 0x33333333u;
+    a = (a | (a >> 2)) & 0x0F0F0F0Fu;
+    b = (b | (b >> 2)) & 0x0F0F0F0Fu;
+    a = (a | (a >> 4)) & 0x00FF00FFu;
+    b = (b | (b >> 4)) & 0x00FF00FFu;
+    a = (a | (a >> 8)) & 0x0000FFFFu;
+    b = (b | (b >> 8)) & 0x0000FFFFu;
+    return a | (b << 16);
 }
 
 // Decisions of positions [i0, i0 + 32) of snapshot column c.
@@ -322,8 +367,13 @@ template <int M>
 __device__ __forceinline__ uint32_t snap_word(const uint8_t* hd, int c, int i0)
 {
     const uint8_t* row = hd + c * Geo<M>::HDS;
-    if constexpr (natural_rows<M>()) return reinterpret_cast<const uint32_t*>(row)[i0 >> 5];
-    else return hd_word(row, snap_lo<M>(c), i0);
+    if constexpr (natural_rows<M>()) {
+        const int lo = snap_lo<M>(c);
+        if (lo == 0) return reinterpret_cast<const uint32_t*>(row)[i0 >> 5];
+        return raw_word(reinterpret_cast<const uint32_t*>(row), lo, i0);
+    } else {
+        return hd_word(row, snap_lo<M>(c), i0);
+    }
 }
 
 template <int RW>
@@ -948,86 +998,34 @@ __device__ __forceinline__ void store_L(Regs<M>& rg, Smem<M>& sm, int e, int pb,
     }
 }
 
-// Snapshot rows: the hard decisions of one column, written by the phase PH
-// that computes it, in natural order for N >= 256 (one byte per thread for
-// smaller codes).  Phase PH maps element e of thread t to position
-// (t & (2^lo - 1)) | e << lo | (t >> lo) << (lo + 3):
-//   lo >= 5: the lanes of a warp cover 32 consecutive positions of each
-//            element, so one ballot per element is a word;
-//   lo = 4, 3: a word takes 16 (8) lanes of two (four) elements' ballots,
-//            assembled with byte permutes by lanes 0..7 (one word each);
-//   lo = 2, 1: a word is four consecutive threads' decisions, spread to their
-//            bit positions and or-ed across the four lanes;
-//   lo = 0: each thread's byte is 8 consecutive positions.
+// Snapshot rows: the hard decisions of one column, written by the phase PH that
+// computes it.  For N >= 256 the phases with register bits from bit lo >= 1
+// write raw ballots (raw_word reads them): one ballot of the warp's decisions
+// per element, the warp's 8 words stored by its lane 0 as two 16-byte stores.
+// The last phase (lo = 0) and smaller codes write one byte per thread (bit e =
+// element e), which for lo = 0 is natural order.
 template <int M, int PH>
-__host__ __device__ constexpr bool ballot_row()
+__host__ __device__ constexpr bool raw_row()
 {
-    return natural_rows<M>() && Geo<M>::lo(PH) >= 3;
+    return natural_rows<M>() && Geo<M>::lo(PH) >= 1;
 }
 
-// Rows of phases with lo >= 3, from the ballots b[e] of the warp's decisions on
-// element e (taken straight from the comparisons by the caller).
 template <int M, int PH>
-__device__ __forceinline__ void snap_row_b(uint8_t* row, const uint32_t (&b)[8], int tid)
+__device__ __forceinline__ void snap_row_raw(uint8_t* row, const uint32_t (&b)[8], int tid)
 {
-    constexpr int lo = Geo<M>::lo(PH);
-    static_assert(ballot_row<M, PH>(), "ballot rows only");
-    uint32_t* w = reinterpret_cast<uint32_t*>(row);
-    const int lane = tid & 31, k = tid >> 5;
-    if constexpr (lo >= 5) {
-        if (lane == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) w[elem_index<M, PH>(tid & ~31, e) >> 5] = b[e];
-        }
-    } else if constexpr (lo == 4) {
-        // word (e >> 1) | (2k + h) << 2 holds lanes 16h.. of elements 2(e>>1) and 2(e>>1)+1
-        if (lane < 8) {
-            const int eh = lane & 3, h = lane >> 2;
-            const uint32_t b0 = eh == 0 ? b[0] : eh == 1 ? b[2] : eh == 2 ? b[4] : b[6];
-            const uint32_t b1 = eh == 0 ? b[1] : eh == 1 ? b[3] : eh == 2 ? b[5] : b[7];
-            w[eh | ((2 * k + h) << 2)] = __byte_perm(b0, b1, h ? 0x7632u : 0x5410u);
-        }
-    } else {
-        // lo = 3: word (e >> 2) | (4k + g) << 1 holds byte g of elements 4(e>>2) .. +3
-        if (lane < 8) {
-            const int eh = lane >> 2, g = lane & 3;
-            const uint32_t b0 = eh ? b[4] : b[0], b1 = eh ? b[5] : b[1];
-            const uint32_t b2 = eh ? b[6] : b[2], b3 = eh ? b[7] : b[3];
-            const uint32_t sel = (uint32_t)g | ((uint32_t)(4 + g) << 4);
-            w[eh | ((4 * k + g) << 1)] = __byte_perm(__byte_perm(b0, b1, sel), __byte_perm(b2, b3, sel), 0x5410u);
-        }
+    static_assert(raw_row<M, PH>(), "raw ballot rows only");
+    if ((tid & 31) == 0) {
+        uint4* d = reinterpret_cast<uint4*>(row + 32 * (tid >> 5));
+        d[0] = make_uint4(b[0], b[1], b[2], b[3]);
+        d[1] = make_uint4(b[4], b[5], b[6], b[7]);
     }
 }
 
-// Rows of the other phases, from each thread's byte of decisions (bit e =
-// element e).
 template <int M, int PH>
 __device__ __forceinline__ void snap_row(uint8_t* row, uint32_t byte, int tid)
 {
-    constexpr int lo = Geo<M>::lo(PH);
-    static_assert(!ballot_row<M, PH>(), "rows with lo >= 3 are built from ballots");
-    if constexpr (lo == 0 || !natural_rows<M>()) {
-        row[tid] = (uint8_t)byte;
-    } else {
-        uint32_t* w = reinterpret_cast<uint32_t*>(row);
-        uint32_t x = byte;
-        if constexpr (lo == 2) {
-            // bit e -> 4e + (t & 3)
-            x = (x | (x << 12)) & 0x000F000Fu;
-            x = (x | (x << 6)) & 0x03030303u;
-            x = (x | (x << 3)) & 0x11111111u;
-            x <<= (tid & 3);
-        } else {
-            // lo = 1: bit e -> 2e + (t & 1) + 16 ((t >> 1) & 1)
-            x = (x | (x << 4)) & 0x0F0Fu;
-            x = (x | (x << 2)) & 0x3333u;
-            x = (x | (x << 1)) & 0x5555u;
-            x <<= (tid & 1) + 16 * ((tid >> 1) & 1);
-        }
-        x |= __shfl_xor_sync(kFull, x, 1);
-        x |= __shfl_xor_sync(kFull, x, 2);
-        if ((tid & 3) == 0) w[tid >> 2] = x;
-    }
+    static_assert(!raw_row<M, PH>(), "byte rows only");
+    row[tid] = (uint8_t)byte;
 }
 
 // Stage s of phase PH.  With XC > 0 the sweep is the lower M stages of a code
@@ -1096,7 +1094,7 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         store_L<M, PH, s, XC>(rg, sm, e, pb_out, nLa, covered);
         store_L<M, PH, s, XC>(rg, sm, e2, pb_out, nLb, covered);
         if constexpr (s == 0 && GSTOP && XC == 0) {
-            if constexpr (ballot_row<M, PH>()) {
+            if constexpr (raw_row<M, PH>()) {
                 xb[e] = __ballot_sync(kFull, __fadd_rn(Ra, nLa) < 0.f);
                 xb[e2] = __ballot_sync(kFull, __fadd_rn(Rb, nLb) < 0.f);
             } else {
@@ -1112,27 +1110,15 @@ __device__ __forceinline__ void run_stage(Regs<M>& rg, Smem<M>& sm, int tid, int
         rg.R[e2] = nRb;
     }
     if constexpr (s == 0 && GSTOP && XC == 0) {
-        if constexpr (ballot_row<M, PH>()) snap_row_b<M, PH>(sm.hd, xb, tid);
+        if constexpr (raw_row<M, PH>()) snap_row_raw<M, PH>(sm.hd, xb, tid);
         else snap_row<M, PH>(sm.hd, xbyte, tid);
     }
     if constexpr (snap) {
-        if constexpr (ballot_row<M, PH>()) {
+        if constexpr (raw_row<M, PH>()) {
             uint32_t b[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) b[e] = __ballot_sync(kFull, rg.R[e] < 0.f);
-            snap_row_b<M, PH>(sm.hd + (s + 1) * G::HDS, b, tid);
-        } else if constexpr (natural_rows<M>() && (G::lo(PH) == 1 || G::lo(PH) == 2)) {
-            // the decisions spread straight to their bits in the natural-order word
-            // that four consecutive threads share (see snap_row)
-            constexpr int LO = G::lo(PH);
-            uint32_t x = 0;
-#pragma unroll
-            for (int e = 0; e < EL; ++e) x |= (rg.R[e] < 0.f ? 1u : 0u) << (e << LO);
-            if constexpr (LO == 2) x <<= (tid & 3);
-            else x <<= (tid & 1) + 16 * ((tid >> 1) & 1);
-            x |= __shfl_xor_sync(kFull, x, 1);
-            x |= __shfl_xor_sync(kFull, x, 2);
-            if ((tid & 3) == 0) reinterpret_cast<uint32_t*>(sm.hd + (s + 1) * G::HDS)[tid >> 2] = x;
+            snap_row_raw<M, PH>(sm.hd + (s + 1) * G::HDS, b, tid);
         } else {
             uint32_t byte = 0;
 #pragma unroll
