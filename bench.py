@@ -37,14 +37,50 @@ ALPHA = 0.9375
 EBN0 = 3.0
 MAX_ITER = 60
 SEED = 1505049790
-# Issue-slot ceiling of the PE update: 152 SMs x 128 lanes x 2070 MHz, 15 lane
-# instructions per PE (3 adds, 3 min-magnitude selections, 3 scalings by alpha,
-# 6 sign operations); see the design notes.
-SMS, LANES, SM_MAX_HZ, OPS_PER_PE = 152, 128, 2.07e9, 15
+# Issue-slot ceiling of the PE update: SMs x 128 lanes (4 schedulers x 32) x the
+# maximum SM clock, over 15 lane instructions per PE update -- Eq. (1) with the
+# min-sum f is 3 adds, 3 min-magnitude selections, 3 scalings by alpha and 3 sign
+# products each merged into the magnitude by one logic operation.  The SM count
+# is read from the device and the clock from MEASURED_PEAKS.json when they are
+# available (GB300: 152 SMs, 2070 MHz).
+LANES, OPS_PER_PE = 128, 15
+SMS, SM_MAX_HZ = 152, 2.07e9
+
+
+def _device_constants():
+    """SM count of cuda:0 and the measured maximum SM clock, when available."""
+    global SMS, SM_MAX_HZ, PEAK_PE_PER_S
+    try:
+        import torch
+        if torch.cuda.is_available():
+            SMS = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        pass
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = json.load(fh).get("sm_max_mhz")
+        if mhz:
+            SM_MAX_HZ = float(mhz) * 1e6
+    except (OSError, ValueError):
+        pass
+    PEAK_PE_PER_S = SMS * LANES * SM_MAX_HZ / OPS_PER_PE
+
+
 PEAK_PE_PER_S = SMS * LANES * SM_MAX_HZ / OPS_PER_PE
-MODES = {"fixed": (0, 0), "gstop": (1, 0), "gstop_freeze": (1, 1)}
-PROFILE = os.path.join(ROOT, "profiles", "bp_decode_n1024_ebn0_3db.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1505_04979_gb300", "csrc", "bp_decode.cuh")
+# (stop_mode, freeze_mode): plain BP with fixed iterations (the paper's baseline [14]), the
+# G-matrix stop ([18]), freezing alone (the paper's proposed method: decoding ends when every
+# CSFG is frozen or at max_iter), and both
+MODES = {"fixed": (0, 0), "gstop": (1, 0), "freeze": (0, 1), "gstop_freeze": (1, 1)}
+PROFILE = os.path.join(ROOT, "profiles", "bp_decode_pipe_n1024_ebn0_3db.md")
+# the headline kernel's sources: the pipelined decoder and the sweep it shares
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1505_04979_gb300", "csrc", f) for f in ("bp_pipe.cuh", "bp_decode.cuh")]
+
+
+def kernel_source_sha256() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def wilson(k: int, n: int, z: float = 1.96):
@@ -67,8 +103,7 @@ def kernel_traffic():
     m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_tr:
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
-    return float(m_tr.group(1)) if sha == m_sha.group(1) else None
+    return float(m_tr.group(1)) if kernel_source_sha256() == m_sha.group(1) else None
 
 
 class ClockSampler:
@@ -391,7 +426,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": PEAK_PE_PER_S / 1e9, "unit": "GPE/s",
                      "frac": achieved / PEAK_PE_PER_S,
                      "traffic": None if traffic is None else traffic,
-                     "kernel": "bp_decode_kernel<10, GSTOP, FREEZE>",
+                     "kernel": "bp_decode_pipe_kernel<10, GSTOP>",
                      "peak_basis": (f"{SMS} SMs x {LANES} lanes x {SM_MAX_HZ / 1e6:.0f} MHz / {OPS_PER_PE} "
                                     "lane instructions per PE update"),
                      "algorithmic_bytes_per_launch": batch * (4 * N + N + 12)},
@@ -511,10 +546,11 @@ def run_mixed(args):
 
 
 def run_sweep(args):
-    """FER sweep of the (1024,512) code: Eb/N0 1.0 .. 3.5 dB in 0.5 dB steps, the three modes
-    (fixed iterations, G-matrix stop, G-matrix stop + CSFG freezing) at max 60 iterations on the
-    same codewords, 10^6 codewords per point (device generator), and the three modes at max 40
-    iterations at 3.0 dB (the paper's setting)."""
+    """FER sweep of the (1024,512) code: Eb/N0 1.0 .. 3.5 dB in 0.5 dB steps, the four modes
+    (fixed iterations, G-matrix stop, freezing alone, G-matrix stop + freezing) at max 60
+    iterations on the same codewords, 10^6 codewords per point (device generator), and the four
+    modes at max 40 iterations at 2.5 / 3.0 / 3.5 dB (the paper's setting is 40 at 3 dB), with
+    freezing's iteration and PE-update changes against plain BP and the G-matrix stop."""
     import torch
     from paper_1505_04979_gb300 import binding as B
     from paper_1505_04979_gb300 import build
@@ -526,10 +562,10 @@ def run_sweep(args):
     uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
     it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
     pe = torch.empty(n_cw, dtype=torch.int64, device="cuda")
-    modes = {"fixed": (0, 0), "gstop": (1, 0), "gstop_freeze": (1, 1)}
+    modes = MODES
     points = []
     with ClockSampler(0) as clk:
-        for eb, mi in [(e, MAX_ITER) for e in (1.0, 1.5, 2.0, 2.5, 3.0, 3.5)] + [(3.0, 40)]:
+        for eb, mi in [(e, MAX_ITER) for e in (1.0, 1.5, 2.0, 2.5, 3.0, 3.5)] + [(e, 40) for e in (2.5, 3.0, 3.5)]:
             u, llr = B.polarbp_awgn(code, SEED + 7, 0, n_cw, eb)
             row = {"ebn0_db": eb, "max_iter": mi, "codewords": n_cw}
             for name, mode in modes.items():
@@ -548,6 +584,12 @@ def run_sweep(args):
                              "avg_iters": float(it.double().mean().item()), "pe_per_codeword": pe_sum / n_cw,
                              "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9, "ms": ms,
                              "alu_frac": pe_sum / (ms * 1e-3) / PEAK_PE_PER_S}
+            # the paper's comparison (Sec. IV): freezing against plain BP with max_iter fixed
+            # iterations and against the G-matrix stop, in average iterations and PE updates
+            row["freeze_vs_fixed"] = {"iterations": row["freeze"]["avg_iters"] / row["fixed"]["avg_iters"] - 1.0,
+                                      "pe_updates": row["freeze"]["pe_per_codeword"] / row["fixed"]["pe_per_codeword"] - 1.0}
+            row["freeze_vs_gstop"] = {"iterations": row["freeze"]["avg_iters"] / row["gstop"]["avg_iters"] - 1.0,
+                                      "pe_updates": row["freeze"]["pe_per_codeword"] / row["gstop"]["pe_per_codeword"] - 1.0}
             points.append(row)
             del u, llr
             torch.cuda.empty_cache()
@@ -555,7 +597,7 @@ def run_sweep(args):
             "value": next(p for p in points if p["ebn0_db"] == 3.0 and p["max_iter"] == MAX_ITER)["gstop_freeze"]["info_gbit_s"],
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"(1024,512) code, {n_cw} codewords per point, alpha {ALPHA}, device generator"},
-            "points": points, "clocks": clk.summary(), "gpu_launches": 2 * 3 * len(points)}
+            "points": points, "clocks": clk.summary(), "gpu_launches": 2 * len(modes) * len(points)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -683,6 +725,12 @@ def run_readings(args):
                              "avg_iters": float(it.double().mean().item()), "pe_per_codeword": pe_sum / n_cw,
                              "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9, "ms": ms,
                              "alu_frac": pe_sum / (ms * 1e-3) / PEAK_PE_PER_S}
+            # the paper's comparison (Sec. IV): freezing against plain BP with max_iter fixed
+            # iterations and against the G-matrix stop, in average iterations and PE updates
+            row["freeze_vs_fixed"] = {"iterations": row["freeze"]["avg_iters"] / row["fixed"]["avg_iters"] - 1.0,
+                                      "pe_updates": row["freeze"]["pe_per_codeword"] / row["fixed"]["pe_per_codeword"] - 1.0}
+            row["freeze_vs_gstop"] = {"iterations": row["freeze"]["avg_iters"] / row["gstop"]["avg_iters"] - 1.0,
+                                      "pe_updates": row["freeze"]["pe_per_codeword"] / row["gstop"]["pe_per_codeword"] - 1.0}
             points.append(row)
             del u, llr
             torch.cuda.empty_cache()
@@ -738,6 +786,12 @@ def run_quantized(args):
                              "avg_iters": float(it.double().mean().item()), "ms": ms,
                              "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9,
                              "pe_per_s": pe_sum / (ms * 1e-3), "alu_frac": pe_sum / (ms * 1e-3) / PEAK_PE_PER_S}
+            # the paper's comparison (Sec. IV): freezing against plain BP with max_iter fixed
+            # iterations and against the G-matrix stop, in average iterations and PE updates
+            row["freeze_vs_fixed"] = {"iterations": row["freeze"]["avg_iters"] / row["fixed"]["avg_iters"] - 1.0,
+                                      "pe_updates": row["freeze"]["pe_per_codeword"] / row["fixed"]["pe_per_codeword"] - 1.0}
+            row["freeze_vs_gstop"] = {"iterations": row["freeze"]["avg_iters"] / row["gstop"]["avg_iters"] - 1.0,
+                                      "pe_updates": row["freeze"]["pe_per_codeword"] / row["gstop"]["pe_per_codeword"] - 1.0}
             points.append(row)
             del u, llr
             torch.cuda.empty_cache()
@@ -971,6 +1025,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    _device_constants()
     if args.workload == "mixed":
         return run_mixed(args)
     if args.workload == "wms":

@@ -126,7 +126,10 @@ int polarbp_encode(const polarbp_code* code, const uint8_t* u, uint8_t* x, int b
  *                stage" as coming only after a failing check: a CSFG that passes
  *                is frozen and the next CSFG of the same stage is checked at
  *                once, on the same R, until one fails.  It is a variant for
- *                comparison (it raises FER sharply, see the design notes);
+ *                comparison: a CSFG checked before its left neighbours' feedback
+ *                has reached it misses the successive-cancellation-like
+ *                decision reading A gives it, and FER rises 13- to 160-fold
+ *                at 2.5-3.5 dB on the (1024,512) code;
  *                N <= 4096, polarbp_decode and polarbp_decode_trace only.
  *   u_hat        device [batch][N] decoded source bits (0 on frozen positions).
  *   iterations   device [batch] int32 iterations run, or NULL.

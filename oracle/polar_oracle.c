@@ -24,8 +24,8 @@
  * the 2^j CSFGs of the paper's stage j, each of size 2^(m-j); CSFG k of level
  * j covers source indices [k 2^(m-j), (k+1) 2^(m-j)) and is fed by R[j].
  *
- * Readings of the paper that this file fixes (every one is also listed in the
- * design notes):
+ * Readings of the paper that this file fixes (the kernels follow the same
+ * readings):
  *   R1  one left-to-right sweep per iteration; R from this iteration, L from
  *       the previous one, exactly as Eq. (1) is written (Sec. II-A).
  *   R2  interior L messages start at 0; L[m] is the prior: +inf on frozen

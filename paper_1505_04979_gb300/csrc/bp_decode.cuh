@@ -29,6 +29,7 @@
 //     messages of covered CSFGs, which nothing reads again.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -1249,6 +1250,43 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
     }
 }
 
+// Stage the channel LLRs of one codeword into shared memory in phase 0's
+// element-major layout (element e of worker t at e * T + t).  With N >= 8 and a
+// 16-byte aligned row the row is read with 16-byte loads, thread i taking
+// positions 4i .. 4i+3, and scattered; otherwise element by element.  Returns
+// false if a loaded value is not finite.  The caller synchronises before the
+// values are read.
+template <int M>
+__device__ __forceinline__ bool stage_llr(float* dst, const float* llr, int tid, int nthreads)
+{
+    using G = Geo<M>;
+    constexpr int N = G::N, T = G::T, lo0 = G::lo(0);
+    bool finite = true;
+    if constexpr (N >= 8) {
+        if ((reinterpret_cast<uintptr_t>(llr) & 15u) == 0) {
+            for (int i = tid; i < N / 4; i += nthreads) {
+                const float4 v = reinterpret_cast<const float4*>(llr)[i];
+                finite &= isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int p = 4 * i + k;
+                    const int t = (p & ((1 << lo0) - 1)) | ((p >> (lo0 + G::RB)) << lo0);
+                    dst[((p >> lo0) & (G::EL - 1)) * T + t] = vv[k];
+                }
+            }
+            return finite;
+        }
+    }
+    for (int p = tid; p < N; p += nthreads) {
+        const float v = llr[p];
+        finite &= isfinite(v);
+        const int t = (p & ((1 << lo0) - 1)) | ((p >> (lo0 + G::RB)) << lo0);
+        dst[((p >> lo0) & (G::EL - 1)) * T + t] = v;
+    }
+    return finite;
+}
+
 // Decode one codeword with the BLOCK threads of group grp (tid = thread index in
 // the group) on the group's shared memory smem_raw.
 template <int M, bool GSTOP, bool FREEZE, bool TRACE, int CPC, bool MULTI = false>
@@ -1278,18 +1316,11 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
         sm.ctl[CTL_EVENT] = 0;
         *sm.pe_acc() = 0;
     }
+    if (!stage_llr<M>(sm.llr, a.llr, tid, G::BLOCK)) atomicOr(status, 1u);
     group_sync<G::BLOCK, CPC>(grp);
 
     Regs<M> rg;
     if (worker) {
-        bool finite = true;
-#pragma unroll
-        for (int e = 0; e < EL; ++e) {
-            const float v = a.llr[elem_index<M, 0>(tid, e)];
-            finite &= isfinite(v);
-            sm.llr[e * T + tid] = v;
-        }
-        if (!finite) atomicOr(status, 1u);
 #pragma unroll
         for (int c = 0; c < G::NRA; ++c)
 #pragma unroll
@@ -1501,18 +1532,28 @@ cudaError_t launch_persistent_one(const SegLaunch& q)
     auto kern = bp_decode_persistent<M, GSTOP, FREEZE, CPC>;
     constexpr size_t smem = SmemLayout<M>::bytes * CPC;
     constexpr int threads = PersistentShape<M, CPC>::THREADS;
-    static int blocks_per_sm = 0;  // one value per instantiation (same on every GB300)
-    if (blocks_per_sm == 0) {
+    // Blocks per SM, one value per device and instantiation, set with the kernel's
+    // shared-memory attribute on the device's first launch.  Host threads that race
+    // on the first launch compute and store the same value.
+    constexpr int kDevices = 64;
+    static std::atomic<int> blocks_per_sm[kDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+    int bps = blocks_per_sm[dev].load(std::memory_order_acquire);
+    if (bps == 0) {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
         int b = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
         if (e != cudaSuccess) return e;
-        blocks_per_sm = b > 0 ? b : 1;
+        bps = b > 0 ? b : 1;
+        blocks_per_sm[dev].store(bps, std::memory_order_release);
     }
-    long long grid = (long long)blocks_per_sm * q.sms;
+    long long grid = (long long)bps * q.sms;
     const long long need = (q.args.total + CPC - 1) / CPC;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;

@@ -445,18 +445,11 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
         sm.ctl[CTL_Q] = 1;
         *sm.pe_acc() = 0;
     }
+    if (!stage_llr<M>(sm.llr, a.llr, tid, THREADS)) atomicOr(args.status, 1u);
     __syncthreads();
 
     if (tid < WORKERS) {
         Regs<M> rg;
-        bool finite = true;
-#pragma unroll
-        for (int e = 0; e < EL; ++e) {
-            const float v = a.llr[elem_index<M, 0>(tid, e)];
-            finite &= isfinite(v);
-            sm.llr[e * T + tid] = v;
-        }
-        if (!finite) atomicOr(args.status, 1u);
 #pragma unroll
         for (int c = 0; c < G::NRA; ++c)
 #pragma unroll
