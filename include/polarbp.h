@@ -90,6 +90,25 @@ void polarbp_destroy(polarbp_code* code);
 /* polarbp_code_info -- N, K and m = log2 N of a handle (any out pointer may be NULL). */
 int polarbp_code_info(const polarbp_code* code, int* N, int* K, int* m);
 
+/*
+ * polarbp_set_bit_reversed -- codeword order of a code handle (Sec. II; Arikan's
+ * generator B_N F^{(x)m}).  With on = 1 the codeword positions travel in
+ * bit-reversed order: channel position i carries code position rev(i), the
+ * m-bit reversal of i, i.e. x = u B_N F^{(x)m} = (u F^{(x)m}) B_N, since B_N
+ * commutes with F^{(x)m}.  The frozen set, the source bits u_hat and every
+ * decoding result keep the natural source order; polarbp_encode writes x in
+ * channel order, polarbp_awgn sends channel order, and polarbp_decode (all its
+ * forms, polarbp_decode_host and polarbp_decode_segments) reads LLRs in channel
+ * order.  The variant decoders (polarbp_decode_flooding, polarbp_decode_quantized,
+ * polarbp_wms_*) reject such a handle with POLARBP_ERR_UNSUPPORTED.  Default 0
+ * (natural order, the paper's Fig. 1).  Not to be changed while work that uses
+ * the handle is in flight.
+ * Errors: POLARBP_ERR_ARG (NULL handle, on not 0 or 1).
+ */
+int polarbp_set_bit_reversed(polarbp_code* code, int on);
+/* polarbp_get_bit_reversed -- the handle's codeword order (0 natural, 1 bit-reversed). */
+int polarbp_get_bit_reversed(const polarbp_code* code, int* on);
+
 /* polarbp_get_frozen_mask -- copy the frozen set to a host array of N bytes (1 = frozen). */
 int polarbp_get_frozen_mask(const polarbp_code* code, uint8_t* frozen_mask);
 

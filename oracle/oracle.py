@@ -69,12 +69,13 @@ def _load():
         lib.orc_decode_q.argtypes = [ci, u8p, f32p, ci, ci, ci, ci, u8p, i32p, i64p, i32p, i32p]
         lib.orc_decode_q_batch.argtypes = [ci, u8p, f32p, ci, ci, ci, ci, ci, ci, u8p, i32p, i64p]
         lib.orc_max_threads.argtypes = []
+        lib.orc_decode_rule_batch.argtypes = [ci, u8p, f32p, ci, ci, cd, ci, ci, cd, ci, ci, u8p, i32p, i64p]
         lib.orc_wms_forward.argtypes = [ci, u8p, f32p, ci, f64p, ci, f64p, f64p, f64p]
         lib.orc_wms_backward.argtypes = [ci, u8p, f32p, ci, f64p, f64p, ci, f64p, f64p]
         for fn in ("orc_bec_lnz", "orc_bec_frozen", "orc_encode", "orc_csfg_check_ext", "orc_decode",
                    "orc_decode_batch", "orc_decode_flood", "orc_decode_flood_batch", "orc_sc_decode",
                    "orc_sc_decode_batch", "orc_decode_q", "orc_decode_q_batch", "orc_max_threads",
-                   "orc_wms_forward", "orc_wms_backward"):
+                   "orc_wms_forward", "orc_wms_backward", "orc_decode_rule_batch"):
             getattr(lib, fn).restype = ci
         _lib = lib
         return lib
@@ -337,3 +338,46 @@ def wms_backward(frozen, llr, weights, dout, fp32: bool = False):
                                     _p(dw, ctypes.c_double),
                                     _p(dl, ctypes.c_double)), "wms_backward")
     return dw, dl
+
+
+RULE_R, RULE_R_PLUS_L, RULE_THRESHOLD = 0, 1, 2
+
+
+def decode_rule_batch(frozen, llr, max_iter: int, alpha: float = 0.9375, stop: int = STOP_NONE, rule: int = RULE_R,
+                      theta: float = 0.0, fp32: bool = False, nthreads: int = 0):
+    """Reading-A freezing with a variant of the CSFG check (rule 0: Eqs. (2)-(4) on R; 1: on R + L;
+    2: on R, only when every |R| of the CSFG is >= theta); returns (u_hat, iters, pe)."""
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    B, N = llr.shape
+    u_hat = np.zeros((B, N), np.uint8)
+    iters = np.zeros(B, np.int32)
+    pe = np.zeros(B, np.int64)
+    _check(_load().orc_decode_rule_batch(N, _p(frozen, ctypes.c_uint8), _p(llr, ctypes.c_float), B, max_iter, alpha,
+                                         stop, rule, theta, 1 if fp32 else 0, nthreads, _p(u_hat, ctypes.c_uint8),
+                                         _p(iters, ctypes.c_int32), _p(pe, ctypes.c_int64)), "decode_rule_batch")
+    return u_hat, iters, pe
+
+
+def bit_reverse_permutation(N: int) -> np.ndarray:
+    """rev[i] = the m-bit reversal of i (N = 2^m): Arikan's B_N as an index map."""
+    m = N.bit_length() - 1
+    i = np.arange(N)
+    r = np.zeros(N, np.int64)
+    for b in range(m):
+        r |= ((i >> b) & 1) << (m - 1 - b)
+    return r
+
+
+def encode_bit_reversed(u: np.ndarray) -> np.ndarray:
+    """x = u B_N F^{(x)m} (Sec. II with Arikan's bit-reversal): channel position i carries
+    position rev(i) of the natural encoding u F^{(x)m}, as B_N F^{(x)m} = F^{(x)m} B_N."""
+    x = encode(u)
+    return np.ascontiguousarray(x[..., bit_reverse_permutation(x.shape[-1])])
+
+
+def natural_order_llr(llr_channel: np.ndarray) -> np.ndarray:
+    """LLRs received in bit-reversed channel order, put back in code-position order (B_N is an
+    involution): decoding a bit-reversed codeword is the natural decode of these."""
+    llr_channel = np.ascontiguousarray(llr_channel)
+    return np.ascontiguousarray(llr_channel[..., bit_reverse_permutation(llr_channel.shape[-1])])

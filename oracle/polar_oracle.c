@@ -239,6 +239,9 @@ typedef struct {
     int64_t pe;
     double margin;
     int nan_seen;
+    int rule;           /* freeze-check variant (orc_decode_rule_batch): 0 = Eqs. (2)-(4) on R */
+    double theta;       /* reliability threshold of rule 2 */
+    double* rl;         /* N: the messages Eq. (2) decides on under rule 1 */
 } dec_t;
 
 #define LM(d, c, i) ((d)->L[(size_t)(c) * (size_t)(d)->N + (size_t)(i)])
@@ -325,6 +328,16 @@ static void check_level(dec_t* d, int j, int multi)
         int base = k * S;
         const double* Rin = &RM(d, j, base);
         for (int i = 0; i < S; ++i) note_margin(d, Rin[i]);
+        if (d->rule == 1) {
+            /* variant: Eq. (2) on the a-posteriori message R + L of the CSFG's input node */
+            for (int i = 0; i < S; ++i) d->rl[i] = rnd(d, Rin[i] + LM(d, j, base + i));
+            Rin = d->rl;
+        } else if (d->rule == 2) {
+            /* variant: Eqs. (2)-(4), and only when every input is at least theta in magnitude */
+            int weak = 0;
+            for (int i = 0; i < S; ++i) weak |= fabs(Rin[i]) < d->theta;
+            if (weak) return;
+        }
         if (!orc_csfg_check(S, Rin, d->frozen + base, d->xh, d->uh, d->scratch)) return;
         freeze_block(d, j, k, d->xh, d->uh);
         if (!multi) return;
@@ -401,9 +414,23 @@ static int gmatrix_stop(dec_t* d, int use_store)
  *   trace_pe   optional max_iter entries: PE updates in each iteration
  * Returns ORC_OK, or a negative error code.
  */
+static int decode_one(int N, const uint8_t* frozen, const float* llr, int max_iter, double alpha, int stop_mode,
+                      int freeze, int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin,
+                      int32_t* cover, double* trace_L, double* trace_R, int32_t* trace_P, int64_t* trace_pe,
+                      int rule, double theta);
+
 int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, double alpha, int stop_mode,
                int freeze, int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin, int32_t* cover,
                double* trace_L, double* trace_R, int32_t* trace_P, int64_t* trace_pe)
+{
+    return decode_one(N, frozen, llr, max_iter, alpha, stop_mode, freeze, fp32, u_hat, iters, pe, margin, cover,
+                      trace_L, trace_R, trace_P, trace_pe, 0, 0.0);
+}
+
+static int decode_one(int N, const uint8_t* frozen, const float* llr, int max_iter, double alpha, int stop_mode,
+                      int freeze, int fp32, uint8_t* u_hat, int32_t* iters, int64_t* pe, double* margin,
+                      int32_t* cover, double* trace_L, double* trace_R, int32_t* trace_P, int64_t* trace_pe,
+                      int rule, double theta)
 {
     int m = ilog2_exact(N);
     if (m < 1 || !frozen || !llr || max_iter < 1 || !(alpha > 0.0) || !u_hat) return ORC_ERR_ARG;
@@ -425,8 +452,11 @@ int orc_decode(int N, const uint8_t* frozen, const float* llr, int max_iter, dou
     d.scratch = (uint8_t*)malloc((size_t)N);
     d.ubits = (uint8_t*)malloc((size_t)N);
     d.xbits = (uint8_t*)malloc((size_t)N);
+    d.rl = (double*)malloc(sizeof(double) * (size_t)N);
+    d.rule = rule;
+    d.theta = theta;
     int rc = ORC_OK;
-    if (!d.L || !d.R || !d.blk || !d.ustore || !d.xh || !d.uh || !d.scratch || !d.ubits || !d.xbits) {
+    if (!d.L || !d.R || !d.blk || !d.ustore || !d.xh || !d.uh || !d.scratch || !d.ubits || !d.xbits || !d.rl) {
         rc = ORC_ERR_NOMEM;
         goto out;
     }
@@ -484,7 +514,43 @@ out:
     free(d.scratch);
     free(d.ubits);
     free(d.xbits);
+    free(d.rl);
     return rc;
+}
+
+/*
+ * orc_decode_rule_batch -- reading A (freeze = 1) with a variant of the CSFG
+ * check, for the comparison of freezing rules the paper leaves open (Sec. III):
+ *   rule 0  Eqs. (2)-(4) on R (the reading every other entry point uses);
+ *   rule 1  Eq. (2) on R + L at the CSFG's input node instead of R;
+ *   rule 2  Eqs. (2)-(4) on R, and only when every |R| of the CSFG is >= theta.
+ * Other arguments as orc_decode_batch (no margins, no cover).
+ */
+int orc_decode_rule_batch(int N, const uint8_t* frozen, const float* llr, int batch, int max_iter, double alpha,
+                          int stop_mode, int rule, double theta, int fp32, int nthreads, uint8_t* u_hat,
+                          int32_t* iters, int64_t* pe)
+{
+    if (batch < 0 || rule < 0 || rule > 2 || !(theta >= 0.0)) return ORC_ERR_ARG;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+#endif
+    for (int c = 0; c < batch; ++c) {
+        int r = decode_one(N, frozen, llr + (size_t)c * (size_t)N, max_iter, alpha, stop_mode, 1, fp32,
+                           u_hat + (size_t)c * (size_t)N, iters ? iters + c : NULL, pe ? pe + c : NULL, NULL, NULL,
+                           NULL, NULL, NULL, NULL, rule, theta);
+        if (r != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            {
+                if (err == ORC_OK) err = r;
+            }
+        }
+    }
+    (void)nthreads;
+    return err;
 }
 
 /*

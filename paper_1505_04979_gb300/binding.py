@@ -46,6 +46,8 @@ _SIGS = {
     "polarbp_destroy": (None, [_VP]),
     "polarbp_code_info": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "polarbp_get_frozen_mask": (ctypes.c_int, [_VP, _VP]),
+    "polarbp_set_bit_reversed": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "polarbp_get_bit_reversed": (ctypes.c_int, [_VP, _VP]),
     "polarbp_encode": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "polarbp_decode": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                       ctypes.c_int, _VP, _VP, _VP, _VP]),
@@ -140,6 +142,15 @@ class PolarCode:
         self.handle = h
         self.N, self.K = N, K
         self.m = N.bit_length() - 1
+
+    def set_bit_reversed(self, on: bool) -> None:
+        """Codeword positions in bit-reversed channel order (polarbp_set_bit_reversed)."""
+        _check(lib().polarbp_set_bit_reversed(self.handle, 1 if on else 0), "polarbp_set_bit_reversed")
+
+    def bit_reversed(self) -> bool:
+        v = ctypes.c_int()
+        _check(lib().polarbp_get_bit_reversed(self.handle, ctypes.byref(v)), "polarbp_get_bit_reversed")
+        return bool(v.value)
 
     def frozen_mask(self) -> np.ndarray:
         out = np.zeros(self.N, np.uint8)

@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
                   nullptr,
                   TRACE ? a.trace_L + tb0 + (long long)XC * N + base : nullptr,
                   TRACE ? a.trace_R + tb0 + (long long)XC * N + base : nullptr,
-                  nullptr};
+                  nullptr,
+                  0};
 
     // ---- initial state
     for (int w = tid; w < NWL; w += T) {
@@ -337,10 +338,12 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
 #pragma unroll
         for (int e = 0; e < EL; ++e) {
             const int i = e * T + tid;
-            const float v = llr[base + i];
+            // bit-reversed order: code position q was received at channel position rev(q)
+            const int q0 = base + i, q1 = p0 * n + i;
+            const float v = llr[a.bitrev ? (int)(__brev((unsigned)q0) >> (32 - M)) : q0];
             finite &= isfinite(v);
             sm.llr[i] = v;
-            cs.LlrP[i] = llr[p0 * n + i];
+            cs.LlrP[i] = llr[a.bitrev ? (int)(__brev((unsigned)q1) >> (32 - M)) : q1];
         }
         if (!finite) atomicOr(a.status, 1u);
 #pragma unroll

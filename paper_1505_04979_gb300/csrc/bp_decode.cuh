@@ -144,6 +144,7 @@ struct DecodeArgs {
     int batch;
     int max_iter;
     float alpha;
+    int bitrev;  // 1: the codeword positions arrive in bit-reversed order (channel position i carries x[rev(i)])
 };
 
 // Pointers of one codeword (trace pointers already offset to the codeword).
@@ -156,6 +157,7 @@ struct CwIO {
     float* trace_L;                // [max_iter][M+1][N], or NULL
     float* trace_R;
     int32_t* trace_P;              // [max_iter]
+    int bitrev;                    // 1: llr[i] belongs to code position rev(i) (bit reversal of m bits)
 };
 
 enum : int { CTL_P = 0, CTL_DONE = 1, CTL_EVENT = 2, CTL_Q = 3, CTL_PE = 4, CTL_EV = 8 };
@@ -1252,18 +1254,19 @@ __device__ __forceinline__ void trace_L_columns(Regs<M>& rg, Smem<M>& sm, int ti
 
 // Stage the channel LLRs of one codeword into shared memory in phase 0's
 // element-major layout (element e of worker t at e * T + t).  With N >= 8 and a
-// 16-byte aligned row the row is read with 16-byte loads, thread i taking
-// positions 4i .. 4i+3, and scattered; otherwise element by element.  Returns
+// 16-byte aligned row in natural order the row is read with 16-byte loads,
+// thread i taking positions 4i .. 4i+3, and scattered; otherwise element by
+// element (gathered through the bit reversal when the code has it).  Returns
 // false if a loaded value is not finite.  The caller synchronises before the
 // values are read.
 template <int M>
-__device__ __forceinline__ bool stage_llr(float* dst, const float* llr, int tid, int nthreads)
+__device__ __forceinline__ bool stage_llr(float* dst, const float* llr, int tid, int nthreads, int bitrev)
 {
     using G = Geo<M>;
     constexpr int N = G::N, T = G::T, lo0 = G::lo(0);
     bool finite = true;
     if constexpr (N >= 8) {
-        if ((reinterpret_cast<uintptr_t>(llr) & 15u) == 0) {
+        if (!bitrev && (reinterpret_cast<uintptr_t>(llr) & 15u) == 0) {
             for (int i = tid; i < N / 4; i += nthreads) {
                 const float4 v = reinterpret_cast<const float4*>(llr)[i];
                 finite &= isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
@@ -1279,7 +1282,8 @@ __device__ __forceinline__ bool stage_llr(float* dst, const float* llr, int tid,
         }
     }
     for (int p = tid; p < N; p += nthreads) {
-        const float v = llr[p];
+        // bit-reversed order: code position p was received at channel position rev(p)
+        const float v = llr[bitrev ? (int)(__brev((unsigned)p) >> (32 - M)) : p];
         finite &= isfinite(v);
         const int t = (p & ((1 << lo0) - 1)) | ((p >> (lo0 + G::RB)) << lo0);
         dst[((p >> lo0) & (G::EL - 1)) * T + t] = v;
@@ -1316,7 +1320,7 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
         sm.ctl[CTL_EVENT] = 0;
         *sm.pe_acc() = 0;
     }
-    if (!stage_llr<M>(sm.llr, a.llr, tid, G::BLOCK)) atomicOr(status, 1u);
+    if (!stage_llr<M>(sm.llr, a.llr, tid, G::BLOCK, a.bitrev)) atomicOr(status, 1u);
     group_sync<G::BLOCK, CPC>(grp);
 
     Regs<M> rg;
@@ -1401,7 +1405,8 @@ __global__ void __launch_bounds__(Geo<M>::BLOCK, Geo<M>::min_blocks(FREEZE)) bp_
                   a.pe ? a.pe + cw : nullptr,
                   TRACE ? a.trace_L + tb : nullptr,
                   TRACE ? a.trace_R + tb : nullptr,
-                  TRACE ? a.trace_P + cw * a.max_iter : nullptr};
+                  TRACE ? a.trace_P + cw * a.max_iter : nullptr,
+                  a.bitrev};
     decode_codeword<M, GSTOP, FREEZE, TRACE, 1, MULTI>(io, a.max_iter, a.alpha, a.status, smem_raw, threadIdx.x, 0);
 }
 
@@ -1423,6 +1428,7 @@ struct SegArgs {
     uint8_t* u_hat[kMaxSeg];
     int32_t* iters[kMaxSeg];
     int64_t* pe[kMaxSeg];
+    int bitrev[kMaxSeg];  // per segment: its code's positions arrive in bit-reversed order
 };
 
 template <int M, int CPC>
@@ -1460,7 +1466,8 @@ __global__ void __launch_bounds__(PersistentShape<M, CPC>::THREADS, PersistentSh
                       a.pe[sg] ? a.pe[sg] + r : nullptr,
                       nullptr,
                       nullptr,
-                      nullptr};
+                      nullptr,
+                      a.bitrev[sg]};
         decode_codeword<M, GSTOP, FREEZE, false, CPC>(io, a.max_iter, a.alpha, a.status[sg], smem, tid, grp);
     }
 }

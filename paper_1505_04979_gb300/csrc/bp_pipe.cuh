@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long cw = blockIdx.x;
     const CwIO a{args.llr + cw * N, args.frozen_words, args.u_hat + cw * N, args.iters ? args.iters + cw : nullptr,
-                 args.pe ? args.pe + cw : nullptr, nullptr, nullptr, nullptr};
+                 args.pe ? args.pe + cw : nullptr, nullptr, nullptr, nullptr, args.bitrev};
     const int tid = threadIdx.x;
     Smem<M> sm(smem_raw);
 
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
         sm.ctl[CTL_Q] = 1;
         *sm.pe_acc() = 0;
     }
-    if (!stage_llr<M>(sm.llr, a.llr, tid, THREADS)) atomicOr(args.status, 1u);
+    if (!stage_llr<M>(sm.llr, a.llr, tid, THREADS, a.bitrev)) atomicOr(args.status, 1u);
     __syncthreads();
 
     if (tid < WORKERS) {

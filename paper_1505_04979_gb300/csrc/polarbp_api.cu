@@ -24,6 +24,7 @@ struct polarbp_code {
     uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
     unsigned int* d_status = nullptr;
     int cpc = 1;  // codewords per block of the persistent launch
+    int bitrev = 0;  // 1: channel position i carries code position rev(i) (Arikan's B_N)
     // polarbp_decode_host's pipeline, created with the handle so that the call
     // itself creates nothing; `pipe_lock` serialises enqueueing on them
     cudaStream_t pipe[kPipe] = {};
@@ -125,7 +126,7 @@ int check_device(const polarbp_code* c)
 
 // x = u F^{(x)m}: one block per codeword, the N bits in shared memory, one
 // butterfly pass per index bit (v[c] ^= v[c + h] for c with bit h clear).
-__global__ void encode_kernel(const uint8_t* __restrict__ u, uint8_t* __restrict__ x, int N, int m)
+__global__ void encode_kernel(const uint8_t* __restrict__ u, uint8_t* __restrict__ x, int N, int m, int bitrev)
 {
     extern __shared__ uint8_t buf[];
     const long long cw = blockIdx.x;
@@ -137,7 +138,9 @@ __global__ void encode_kernel(const uint8_t* __restrict__ u, uint8_t* __restrict
             if (!(c & h)) buf[c] ^= buf[c + h];
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) x[cw * N + i] = buf[i];
+    // bit-reversed order: channel position i carries code position rev(i)
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        x[cw * N + i] = buf[bitrev ? (int)(__brev((unsigned)i) >> (32 - m)) : i];
 }
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
@@ -169,7 +172,7 @@ __device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint64_t cw, uint
 
 // One block per codeword: source bits, encoder (as encode_kernel), BPSK + AWGN.
 __global__ void awgn_kernel(const uint32_t* __restrict__ frozen_words, int N, int m, uint64_t seed, uint64_t first,
-                            float sigma_all, const float* __restrict__ ebn0_per_cw, float rate,
+                            float sigma_all, const float* __restrict__ ebn0_per_cw, float rate, int bitrev,
                             uint8_t* __restrict__ u_out, float* __restrict__ llr)
 {
     extern __shared__ uint8_t bits[];
@@ -200,9 +203,12 @@ __global__ void awgn_kernel(const uint32_t* __restrict__ frozen_words, int N, in
         const float r = sqrtf(-2.f * logf(u1));
         float sn, cs;
         sincospif(2.f * u2, &sn, &cs);
+        // channel positions i0, i1 carry code positions rev(i0), rev(i1) in bit-reversed order
         const int i0 = 2 * p, i1 = 2 * p + 1;
-        llr[b * N + i0] = scale * ((1.f - 2.f * bits[i0]) + sigma * r * cs);
-        if (i1 < N) llr[b * N + i1] = scale * ((1.f - 2.f * bits[i1]) + sigma * r * sn);
+        const int c0 = bitrev ? (int)(__brev((unsigned)i0) >> (32 - m)) : i0;
+        const int c1 = bitrev ? (int)(__brev((unsigned)i1) >> (32 - m)) : i1;
+        llr[b * N + i0] = scale * ((1.f - 2.f * bits[c0]) + sigma * r * cs);
+        if (i1 < N) llr[b * N + i1] = scale * ((1.f - 2.f * bits[c1]) + sigma * r * sn);
     }
 }
 
@@ -271,6 +277,7 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     q.args.batch = batch;
     q.args.max_iter = max_iter;
     q.args.alpha = scale;
+    q.args.bitrev = c->bitrev;
     q.stop_mode = stop_mode;
     q.freeze_mode = freeze_mode;
     q.trace = trace;
@@ -392,6 +399,7 @@ unsigned int* status_word(const polarbp_code* c) { return c->d_status; }
 int fail(int code, const std::string& msg) { return ::fail(code, msg); }
 int cuda_fail(cudaError_t e, const char* what) { return ::cuda_fail(e, what); }
 int check_device(const polarbp_code* c) { return ::check_device(c); }
+int bit_reversed(const polarbp_code* c) { return c->bitrev; }
 }  // namespace polarbp_internal
 
 // Free everything a code handle owns (any member may still be unset).
@@ -501,6 +509,21 @@ int polarbp_code_info(const polarbp_code* c, int* N, int* K, int* m)
     return POLARBP_OK;
 }
 
+int polarbp_set_bit_reversed(polarbp_code* c, int on)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (on != 0 && on != 1) return fail(POLARBP_ERR_ARG, "on must be 0 or 1");
+    c->bitrev = on;
+    return POLARBP_OK;
+}
+
+int polarbp_get_bit_reversed(const polarbp_code* c, int* on)
+{
+    if (!c || !on) return fail(POLARBP_ERR_ARG, "NULL argument");
+    *on = c->bitrev;
+    return POLARBP_OK;
+}
+
 int polarbp_get_frozen_mask(const polarbp_code* c, uint8_t* frozen_mask)
 {
     if (!c || !frozen_mask) return fail(POLARBP_ERR_ARG, "NULL argument");
@@ -517,7 +540,7 @@ int polarbp_encode(const polarbp_code* c, const uint8_t* u, uint8_t* x, int batc
     int rc = check_device(c);
     if (rc != POLARBP_OK) return rc;
     const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
-    encode_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(u, x, c->N, c->m);
+    encode_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(u, x, c->N, c->m, c->bitrev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "encode launch");
     return POLARBP_OK;
@@ -635,8 +658,8 @@ int polarbp_awgn(const polarbp_code* c, uint64_t seed, uint64_t first_codeword, 
     const float sigma = (float)std::sqrt(1.0 / (2.0 * rate * std::pow(10.0, ebn0_db / 10.0)));
     const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
     awgn_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(c->d_frozen, c->N, c->m, seed,
-                                                                             first_codeword, sigma, nullptr, 0.f, u,
-                                                                             llr);
+                                                                             first_codeword, sigma, nullptr, 0.f,
+                                                                             c->bitrev, u, llr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "awgn launch");
     return POLARBP_OK;
@@ -762,6 +785,7 @@ int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter,
             q.args.u_hat[j] = sg.u_hat;
             q.args.iters[j] = sg.iterations;
             q.args.pe[j] = sg.pe_updates;
+            q.args.bitrev[j] = sg.code->bitrev;
             start += sg.count;
         }
         q.args.start[q.args.nseg] = start;
@@ -853,7 +877,7 @@ int polarbp_awgn_ebn0(const polarbp_code* c, uint64_t seed, uint64_t first_codew
     if (rc != POLARBP_OK) return rc;
     const int threads = c->N < 256 ? (c->N < 32 ? 32 : c->N) : 256;
     awgn_kernel<<<batch, threads, c->N, static_cast<cudaStream_t>(stream)>>>(
-        c->d_frozen, c->N, c->m, seed, first_codeword, 0.f, ebn0_db, (float)c->K / (float)c->N, u, llr);
+        c->d_frozen, c->N, c->m, seed, first_codeword, 0.f, ebn0_db, (float)c->K / (float)c->N, c->bitrev, u, llr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "awgn launch");
     return POLARBP_OK;

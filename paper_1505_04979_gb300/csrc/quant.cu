@@ -185,6 +185,7 @@ unsigned int* status_word(const polarbp_code* c);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 int check_device(const polarbp_code* c);
+int bit_reversed(const polarbp_code* c);
 }  // namespace polarbp_internal
 
 extern "C" {
@@ -207,6 +208,7 @@ int polarbp_decode_quantized(const polarbp_code* code, const float* llr, int bat
     if (m > 10) return fail(POLARBP_ERR_UNSUPPORTED, "quantised messages support N <= 1024");
     if (batch == 0) return POLARBP_OK;
     if (!llr || !u_hat) return fail(POLARBP_ERR_ARG, "llr and u_hat must be device pointers");
+    if (bit_reversed(code)) return fail(POLARBP_ERR_UNSUPPORTED, "this decoder variant takes codewords in natural order only (see polarbp_set_bit_reversed)");
     int rc = check_device(code);
     if (rc != POLARBP_OK) return rc;
     QArgs a;

@@ -259,6 +259,7 @@ const uint32_t* frozen_words(const polarbp_code* c);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 int check_device(const polarbp_code* c);
+int bit_reversed(const polarbp_code* c);
 }  // namespace polarbp_internal
 
 namespace {
@@ -285,6 +286,7 @@ int wms_args(const polarbp_code* c, int batch, int T, int* N, int* m)
     if (T < 1) return fail(POLARBP_ERR_ARG, "iterations must be >= 1");
     polarbp_code_info(c, N, nullptr, m);
     if (*m > 10) return fail(POLARBP_ERR_UNSUPPORTED, "weighted min-sum supports N <= 1024");
+    if (bit_reversed(c)) return fail(POLARBP_ERR_UNSUPPORTED, "this decoder variant takes codewords in natural order only (see polarbp_set_bit_reversed)");
     return POLARBP_OK;
 }
 }  // namespace

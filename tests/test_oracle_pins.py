@@ -620,3 +620,110 @@ def test_quantised_channel_values():
     r = O.decode_q(np.zeros(8, np.uint8), llr, 1, A=15, F=3, trace=True)
     want = np.clip(np.rint(llr.astype(np.float64) * 8), -32767, 32767).astype(np.int64)
     assert r["R"][0][0].tolist() == want.tolist() == [2, -2, 8, 23, -32767, 32767, 0, 0]
+
+
+# ---------------------------------------------------------------------------
+# Freeze-rule variants of the CSFG check (Sec. III leaves the decided message
+# and any reliability condition open); used only for the comparison study.
+# ---------------------------------------------------------------------------
+def _rule_inputs(N, K, batch, ebn0, seed):
+    fz = O.bec_frozen(N, K)
+    idx = np.arange(batch)
+    u = I.info_bits(seed, idx, fz)
+    llr = I.channel_llr(O.encode(u), I.gaussian(seed, idx, N), I.sigma(ebn0, K / N))
+    return fz, u, llr
+
+
+@pytest.mark.parametrize("stop", [0, 1])
+def test_rule_r_is_reading_a(stop):
+    fz, u, llr = _rule_inputs(256, 128, 60, 2.5, 71)
+    a = O.decode_batch(fz, llr, 40, 0.9375, stop, O.FREEZE_CSFG)
+    b = O.decode_rule_batch(fz, llr, 40, 0.9375, stop, O.RULE_R)
+    for x, y in zip(a[:3], b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("stop", [0, 1])
+def test_threshold_rule_limits(stop):
+    """|R| >= 0 always holds (the rule is reading A); no |R| reaches +inf (nothing freezes: the
+    decode is that without freezing, every PE of every iteration counted)."""
+    N, M = 256, 8
+    fz, u, llr = _rule_inputs(N, 128, 40, 2.5, 72)
+    a = O.decode_rule_batch(fz, llr, 30, 0.9375, stop, O.RULE_R)
+    b = O.decode_rule_batch(fz, llr, 30, 0.9375, stop, O.RULE_THRESHOLD, theta=0.0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    c = O.decode_rule_batch(fz, llr, 30, 0.9375, stop, O.RULE_THRESHOLD, theta=float("inf"))
+    d = O.decode_batch(fz, llr, 30, 0.9375, stop, O.FREEZE_OFF)
+    assert np.array_equal(c[0], d[0]) and np.array_equal(c[1], d[1])
+    assert np.array_equal(c[2], c[1].astype(np.int64) * M * N // 2)
+
+
+def test_r_plus_l_rule_first_iteration():
+    """In iteration 1 every interior L is 0, so the checks of stages 1..m-1 see R + L = R: the
+    first iteration's PE count (which depends only on them) equals rule R's."""
+    fz, u, llr = _rule_inputs(512, 256, 50, 2.0, 73)
+    a = O.decode_rule_batch(fz, llr, 1, 0.9375, 0, O.RULE_R)
+    b = O.decode_rule_batch(fz, llr, 1, 0.9375, 0, O.RULE_R_PLUS_L)
+    assert np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("N", [16, 64, 1024])
+def test_r_plus_l_rule_noiseless(N):
+    """Noiseless inputs: R and L agree with the transmitted codeword, every check passes in order,
+    and the decode returns the source word."""
+    fz = O.bec_frozen(N, N // 2)
+    u = I.info_bits(5, np.arange(6), fz)
+    llr = I.noiseless_llr(O.encode(u), 3.0)
+    uh, it, pe = O.decode_rule_batch(fz, llr, 30, 0.9375, 0, O.RULE_R_PLUS_L)
+    assert np.array_equal(uh, u)
+    assert np.all(it <= 2)
+
+
+# ---------------------------------------------------------------------------
+# Bit-reversed codeword order (Arikan's G = B_N F^{(x)m}, Sec. II)
+# ---------------------------------------------------------------------------
+def _bit_reversal_matrix(N):
+    m = N.bit_length() - 1
+    B = np.zeros((N, N), np.int64)
+    for i in range(N):
+        B[i, int(format(i, f"0{m}b")[::-1], 2) if m else 0] = 1
+    return B
+
+
+def _F_kron(N):
+    F = np.array([[1, 0], [1, 1]], np.int64)
+    G = np.array([[1]], np.int64)
+    while G.shape[0] < N:
+        G = np.kron(G, F)
+    return G
+
+
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32])
+def test_bit_reversal_commutes_with_the_kernel(N):
+    """B_N F^{(x)m} = F^{(x)m} B_N over the integers (hence GF(2)), from the matrices' definitions."""
+    B, G = _bit_reversal_matrix(N), _F_kron(N)
+    assert np.array_equal(B @ G, G @ B)
+    assert np.array_equal(B @ B, np.eye(N, dtype=np.int64))
+
+
+@pytest.mark.parametrize("N", [2, 8, 16, 32])
+def test_bit_reversed_encoder_is_arikans_generator(N):
+    rng = np.random.default_rng(N)
+    u = rng.integers(0, 2, (20, N)).astype(np.uint8)
+    want = (u.astype(np.int64) @ (_bit_reversal_matrix(N) @ _F_kron(N))) % 2
+    assert np.array_equal(O.encode_bit_reversed(u), want.astype(np.uint8))
+    rev = O.bit_reverse_permutation(N)
+    assert np.array_equal(rev[rev], np.arange(N))
+
+
+@pytest.mark.parametrize("N", [8, 64, 1024])
+def test_bit_reversed_noiseless_round_trip(N):
+    """Noiseless BPSK of the bit-reversed codeword, put back in code order, decodes to u with the
+    noiseless invariants of the natural order (G-stop at iteration 1, freeze-only at 2)."""
+    fz = O.bec_frozen(N, N // 2)
+    u = I.info_bits(9, np.arange(4), fz)
+    llr = O.natural_order_llr(I.noiseless_llr(O.encode_bit_reversed(u), 3.0))
+    for stop, freeze, iters in ((1, 0, 1), (0, 1, 2), (1, 1, 1)):
+        uh, it, pe, _ = O.decode_batch(fz, llr, 30, 0.9375, stop, freeze)
+        assert np.array_equal(uh, u) and np.all(it == iters)
