@@ -545,6 +545,56 @@ def run_mixed(args):
     return 0
 
 
+def run_bitrev(args):
+    """Natural against bit-reversed codeword order (x = u B_N F^{(x)m}) on the benchmark's code and
+    mode ((1024,512), 3.0 dB, G-matrix stop + CSFG freezing, max 60 iterations), --batch
+    codewords per order from the device generator (the same source bits and noise, the channel
+    positions permuted): FER with Wilson 95 % intervals, average iterations, PE updates per
+    codeword and info Gbit/s.  B_N only permutes the channel positions, so the two rows must
+    agree within their intervals."""
+    import torch
+    from paper_1505_04979_gb300 import binding as B
+    from paper_1505_04979_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n_cw = args.batch
+    rows = {}
+    with ClockSampler(0) as clk:
+        for order in ("natural", "bit_reversed"):
+            code = B.polarbp_construct(N, K)
+            code.set_bit_reversed(order == "bit_reversed")
+            u, llr = B.polarbp_awgn(code, SEED + 13, 0, n_cw, EBN0)
+            uh = torch.empty((n_cw, N), dtype=torch.uint8, device="cuda")
+            it = torch.empty(n_cw, dtype=torch.int32, device="cuda")
+            pe = torch.empty(n_cw, dtype=torch.int64, device="cuda")
+            for _ in range(max(1, args.warmup)):
+                B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, 1, uh, it, pe, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            steps = max(1, min(args.steps, 5))
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, 1, uh, it, pe, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            errs = int((uh != u).any(dim=1).sum().item())
+            rows[order] = {"fer": errs / n_cw, "fer_ci95": list(wilson(errs, n_cw)),
+                           "avg_iters": float(it.double().mean().item()),
+                           "pe_per_codeword": float(pe.double().mean().item()),
+                           "info_gbit_s": n_cw * K / (ms * 1e-3) / 1e9, "ms": ms}
+            del u, llr, uh, it, pe
+            code.close()
+    line = {"metric": "natural vs bit-reversed codeword order, (1024,512) 3.0 dB, G-stop + freezing",
+            "unit": "Gbit/s", "value": rows["bit_reversed"]["info_gbit_s"], "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"(1024,512) code, {n_cw} codewords per order, max {MAX_ITER} iterations"},
+            "orders": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_sweep(args):
     """FER sweep of the (1024,512) code: Eb/N0 1.0 .. 3.5 dB in 0.5 dB steps, the four modes
     (fixed iterations, G-matrix stop, freezing alone, G-matrix stop + freezing) at max 60
@@ -1010,7 +1060,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--sweep-codewords", type=int, default=1000000)
     ap.add_argument("--workload", choices=["n1024", "mixed", "long", "wms", "sweep", "flooding", "readings",
-                                           "quantized"],
+                                           "quantized", "bitrev"],
                     default="n1024",
                     help="n1024: the (1024,512) headline; mixed: the mixed-length stream; long: N = 8192..32768 "
                          "on thread-block clusters; wms: learned weights; sweep: FER over Eb/N0; flooding: the "
@@ -1040,6 +1090,8 @@ def main():
         return run_quantized(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "bitrev":
+        return run_bitrev(args)
     return run_ours(args)
 
 

@@ -267,9 +267,7 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
 #pragma unroll
             for (int h = 1; h < 32; h <<= 1)
                 if (h < Sl) bad |= bad >> h;
-            const uint32_t starts = Sl == 1 ? 0xffffffffu : Sl == 2 ? 0x55555555u : Sl == 4 ? 0x11111111u
-                                  : Sl == 8 ? 0x01010101u : Sl == 16 ? 0x00010001u : 0x00000001u;
-            pw = ~bad & starts;
+            pw = ~bad;  // bit k S: CSFG k of the word passes (the chain reads block starts only)
         }
         uint32_t pa[12];
 #pragma unroll
@@ -347,11 +345,13 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
             const unsigned evm = __reduce_or_sync(kFull, ev ? (1u << jl) : 0u);
             if (lane == 0) sm.ctl[CTL_EVENT] |= (int)evm;
             // shared-memory columns (the boundary columns and column M): one position per lane
+            const bool hi_word = P > 32 * (w0 + 1);  // a frozen CSFG reaches word w0 + 1
 #pragma unroll
             for (int c = JS; c <= M; ++c) {
-                if (smem_column(M, c)) {
+                if (smem_column(M, c) && c >= jf) {
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
+                        if (k == 1 && !hi_word) break;
                         const int src = 2 * (c - JS) + k;
                         const uint32_t m = __shfl_sync(kFull, mc, src);
                         const uint32_t xv = __shfl_sync(kFull, xc, src);
