@@ -500,7 +500,24 @@ def run_mixed(args):
         for code, llr, uh, it, pe in segs:
             B.polarbp_decode(code, llr, MAX_ITER, ALPHA, 1, 1, uh, it, pe, stream=stream)
     ms_plain = timed(per_class, max(3, args.steps // 4))
-    g.replay()
+
+    # the whole stream in one persistent launch (blocks split longest length first)
+    B.polarbp_decode_mixed(segs, MAX_ITER, ALPHA, 1, 1, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    g1 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g1):
+        B.polarbp_decode_mixed(segs, MAX_ITER, ALPHA, 1, 1, workspace=ws, stream=torch.cuda.current_stream())
+    with ClockSampler(0) as clk1:
+        ms_one = timed(g1.replay, args.steps)
+    ms_one_unc = timed(lambda: B.polarbp_decode_mixed(segs, MAX_ITER, ALPHA, 1, 1, workspace=ws, stream=stream),
+                       max(3, args.steps // 4))
+    ms_per_len = ms_graph
+    one_launch = ms_one < ms_graph
+    if one_launch:
+        ms_graph, clk = ms_one, clk1
+        g1.replay()
+    else:
+        g.replay()
     torch.cuda.synchronize()
     per = {}
     pe_total = 0.0
@@ -516,14 +533,20 @@ def run_mixed(args):
             "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"mixed stream, {total} codewords per step, G-matrix stop + CSFG freezing, "
-                                   f"max {MAX_ITER} iterations, persistent launches in one CUDA graph",
+                                   f"max {MAX_ITER} iterations, "
+                                   + ("one persistent launch for all lengths (polarbp_decode_mixed)" if one_launch
+                                      else "one persistent launch per length (polarbp_decode_segments)")
+                                   + " in a CUDA graph, the faster of the two",
                        "codewords_per_block": cpcs},
-            "variants_ms_per_step": {"graph": ms_graph, "persistent_uncaptured": ms_persist,
+            "variants_ms_per_step": {"one_launch_graph": ms_one, "one_launch_uncaptured": ms_one_unc,
+                                     "per_length_graph": ms_per_len,
+                                     "per_length_uncaptured": ms_persist,
                                      "one_block_per_codeword": ms_plain},
             "roofline": {"bound": "alu", "achieved": pe_total / (ms_graph * 1e-3) / 1e9,
                          "peak": PEAK_PE_PER_S / 1e9, "unit": "GPE/s",
                          "frac": pe_total / (ms_graph * 1e-3) / PEAK_PE_PER_S},
-            "classes": per, "clocks": clk.summary(), "gpu_launches": args.steps * len({c[0] for c in MIXED_CLASSES})}
+            "classes": per, "clocks": clk.summary(),
+            "gpu_launches": args.steps * (1 if one_launch else len({c[0] for c in MIXED_CLASSES}))}
     if not args.skip_cpu:
         # the oracle on a sample of the same stream: the first codewords of each class
         from oracle import oracle as O

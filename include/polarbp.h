@@ -351,6 +351,31 @@ size_t polarbp_decode_segments_workspace(void);
 int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
                             int freeze_mode, void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * polarbp_decode_mixed -- the decode of polarbp_decode_segments (Eq. (1) of Sec.
+ * II-A per codeword, G-matrix stop, CSFG freezing of Sec. III) in ONE persistent
+ * launch over every code length of the stream.  A block has the thread count of
+ * the longest length present (N/8 threads, at least a warp) and drains the
+ * per-length device queues longest first; when a length's queue is empty, each
+ * group of threads splits into two groups that take codewords of half that
+ * length in the two halves of its shared memory, down to one warp per N = 256
+ * codeword.  Codewords retire at their own stop, independently of the others.
+ * The codewords-per-block setting of the codes is not used.  The call may be
+ * captured into a CUDA graph after one uncaptured call (the first call per
+ * kernel sets attributes and queries occupancy).
+ *   segs, nseg, max_iter, scale, stop_mode, freeze_mode: as polarbp_decode_segments
+ *                (at most 8 runs per code length, N in {256 .. 4096}).
+ *   workspace    device buffer of polarbp_decode_segments_workspace() bytes
+ *                (counters; zeroed by the call, on `stream`).  Calls sharing a
+ *                workspace must not overlap on the GPU.
+ *   stream       the launch's stream; nothing runs on other streams.
+ * Output and iteration / PE counts are those of polarbp_decode, codeword by
+ * codeword; a non-finite LLR sets the status word of its own segment's code.
+ * Errors: POLARBP_ERR_ARG, POLARBP_ERR_UNSUPPORTED (N < 256 or > 4096), POLARBP_ERR_CUDA.
+ */
+int polarbp_decode_mixed(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
+                         int freeze_mode, void* workspace, size_t workspace_bytes, void* stream);
+
 /* polarbp_set_codewords_per_block / polarbp_get_codewords_per_block -- codewords
  * decoded side by side by one block of the persistent launch (1, 2 or 4, as
  * thread and shared-memory limits allow for the code length). */

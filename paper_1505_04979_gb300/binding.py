@@ -68,6 +68,8 @@ _SIGS = {
     "polarbp_decode_segments_workspace": (ctypes.c_size_t, []),
     "polarbp_decode_segments": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                                ctypes.c_int, _VP, ctypes.c_size_t, _VP]),
+    "polarbp_decode_mixed": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                            ctypes.c_int, _VP, ctypes.c_size_t, _VP]),
     "polarbp_set_codewords_per_block": (ctypes.c_int, [_VP, ctypes.c_int]),
     "polarbp_get_codewords_per_block": (ctypes.c_int, [_VP, _VP]),
     "polarbp_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _VP]),
@@ -228,10 +230,7 @@ def polarbp_decode_segments_workspace() -> int:
     return int(lib().polarbp_decode_segments_workspace())
 
 
-def polarbp_decode_segments(segments, max_iter: int, scale: float = 0.9375, stop_mode: int = 0,
-                            freeze_mode: int = 0, workspace=None, stream=None):
-    """Decode runs of codewords [(code, llr, u_hat, iterations, pe_updates), ...] with one
-    persistent launch per code length.  ``workspace``: CUDA uint8 tensor (allocated if None)."""
+def _segment_array(segments):
     import torch
     arr = (_Segment * max(1, len(segments)))()
     for k, (code, llr, u_hat, it, pe) in enumerate(segments):
@@ -244,11 +243,34 @@ def polarbp_decode_segments(segments, max_iter: int, scale: float = 0.9375, stop
             _need(pe, torch.int64, (n,), "pe_updates")
         arr[k] = _Segment(code.handle.value, llr.data_ptr(), u_hat.data_ptr(), None if it is None else it.data_ptr(),
                           None if pe is None else pe.data_ptr(), n)
+    return arr
+
+
+def polarbp_decode_segments(segments, max_iter: int, scale: float = 0.9375, stop_mode: int = 0,
+                            freeze_mode: int = 0, workspace=None, stream=None):
+    """Decode runs of codewords [(code, llr, u_hat, iterations, pe_updates), ...] with one
+    persistent launch per code length.  ``workspace``: CUDA uint8 tensor (allocated if None)."""
+    import torch
+    arr = _segment_array(segments)
     if workspace is None:
         workspace = torch.empty(polarbp_decode_segments_workspace(), dtype=torch.uint8, device="cuda")
     _check(lib().polarbp_decode_segments(ctypes.cast(arr, ctypes.c_void_p), len(segments), max_iter, scale,
                                          stop_mode, freeze_mode, _ptr(workspace), workspace.numel(),
                                          _stream(stream)), "polarbp_decode_segments")
+    return workspace
+
+
+def polarbp_decode_mixed(segments, max_iter: int, scale: float = 0.9375, stop_mode: int = 0,
+                         freeze_mode: int = 0, workspace=None, stream=None):
+    """Decode runs of codewords [(code, llr, u_hat, iterations, pe_updates), ...] of mixed
+    lengths with ONE persistent launch.  ``workspace``: CUDA uint8 tensor (allocated if None)."""
+    import torch
+    arr = _segment_array(segments)
+    if workspace is None:
+        workspace = torch.empty(polarbp_decode_segments_workspace(), dtype=torch.uint8, device="cuda")
+    _check(lib().polarbp_decode_mixed(ctypes.cast(arr, ctypes.c_void_p), len(segments), max_iter, scale,
+                                      stop_mode, freeze_mode, _ptr(workspace), workspace.numel(),
+                                      _stream(stream)), "polarbp_decode_mixed")
     return workspace
 
 

@@ -1,0 +1,9 @@
+// One-launch mixed-stream decoder whose longest code length is 2^10 (bp_mixed.cuh).
+#include "bp_mixed.cuh"
+
+namespace polarbp {
+cudaError_t launch_mixed_m10(const MixedArgs& a, int stop_mode, int freeze_mode, int sms, cudaStream_t s)
+{
+    return launch_mixed<10>(a, stop_mode, freeze_mode, sms, s);
+}
+}  // namespace polarbp

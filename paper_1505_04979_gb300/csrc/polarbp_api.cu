@@ -14,6 +14,7 @@
 
 #include "polarbp.h"
 #include "bp_decode.cuh"
+#include "bp_mixed.cuh"
 
 constexpr int kPipe = 3;  // streams of polarbp_decode_host's copy/decode pipeline
 
@@ -55,6 +56,11 @@ cudaError_t launch_persistent_m9(const SegLaunch&);
 cudaError_t launch_persistent_m10(const SegLaunch&);
 cudaError_t launch_persistent_m11(const SegLaunch&);
 cudaError_t launch_persistent_m12(const SegLaunch&);
+cudaError_t launch_mixed_m8(const MixedArgs&, int, int, int, cudaStream_t);  // one launch, longest N = 2^m (bp_mixed.cuh)
+cudaError_t launch_mixed_m9(const MixedArgs&, int, int, int, cudaStream_t);
+cudaError_t launch_mixed_m10(const MixedArgs&, int, int, int, cudaStream_t);
+cudaError_t launch_mixed_m11(const MixedArgs&, int, int, int, cudaStream_t);
+cudaError_t launch_mixed_m12(const MixedArgs&, int, int, int, cudaStream_t);
 }  // namespace polarbp
 
 namespace {
@@ -387,6 +393,76 @@ int noalloc_scratch_address(void** out)
         g_noalloc_addr[dev] = p;
     }
     *out = g_noalloc_addr[dev];
+    return POLARBP_OK;
+}
+
+
+int first_of_length(const polarbp_segment* segs, int nseg, int m)
+{
+    for (int k = 0; k < nseg; ++k)
+        if (segs[k].count > 0 && segs[k].code->m == m) return k;
+    return 0;
+}
+
+// Checks the arguments of the mixed-stream entry points and groups the runs by
+// code length: args[m] (m = 8 .. 12) lists the runs of length 2^m in call order,
+// their queue counter at workspace + m; total 0 when the stream has none.
+// per_length: the runs are decoded by one persistent launch per length, whose
+// codewords-per-block setting must be admissible.
+int group_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode, int freeze_mode,
+                   void* workspace, size_t workspace_bytes, bool per_length, polarbp::SegArgs* args)
+{
+    if (nseg < 0 || (nseg > 0 && !segs)) return fail(POLARBP_ERR_ARG, "bad segment list");
+    if (max_iter < 1) return fail(POLARBP_ERR_ARG, "max_iter must be >= 1");
+    if (!(scale > 0.f) || !std::isfinite(scale)) return fail(POLARBP_ERR_ARG, "scale must be finite and > 0");
+    if (stop_mode != POLARBP_STOP_NONE && stop_mode != POLARBP_STOP_GMATRIX)
+        return fail(POLARBP_ERR_ARG, "unknown stop_mode");
+    if (freeze_mode != POLARBP_FREEZE_OFF && freeze_mode != POLARBP_FREEZE_CSFG)
+        return fail(POLARBP_ERR_ARG, "unknown freeze_mode");
+    if (!workspace || workspace_bytes < (size_t)kSegWorkspace) return fail(POLARBP_ERR_ARG, "workspace too small");
+    std::vector<int> by_m[13];
+    for (int k = 0; k < nseg; ++k) {
+        const polarbp_segment& g = segs[k];
+        if (!g.code) return fail(POLARBP_ERR_ARG, "segment without a code");
+        if (g.code->m < 8 || g.code->m > 12)
+            return fail(POLARBP_ERR_UNSUPPORTED, "segments support N from 256 to 4096");
+        if (g.count < 0) return fail(POLARBP_ERR_ARG, "segment count must be >= 0");
+        if (g.count == 0) continue;
+        if (!g.llr || !g.u_hat) return fail(POLARBP_ERR_ARG, "segment llr and u_hat must be device pointers");
+        int rc = check_device(g.code);
+        if (rc != POLARBP_OK) return rc;
+        by_m[g.code->m].push_back(k);
+    }
+    for (int m = 0; m <= 12; ++m) {
+        polarbp::SegArgs& q = args[m];
+        q = polarbp::SegArgs{};
+        q.queue = static_cast<int*>(workspace) + m;
+        q.max_iter = max_iter;
+        q.alpha = scale;
+        if (by_m[m].empty()) continue;
+        if ((int)by_m[m].size() > polarbp::kMaxSeg) return fail(POLARBP_ERR_ARG, "at most 8 segments per code length");
+        long long total = 0;
+        for (int k : by_m[m]) total += segs[k].count;
+        if (total > 0x7fffffffLL) return fail(POLARBP_ERR_ARG, "too many codewords of one length");
+        if (per_length && !polarbp::persistent_supported(m, segs[by_m[m][0]].code->cpc))
+            return fail(POLARBP_ERR_UNSUPPORTED, "codewords per block");
+        q.nseg = (int)by_m[m].size();
+        int start = 0;
+        for (int j = 0; j < q.nseg; ++j) {
+            const polarbp_segment& sg = segs[by_m[m][j]];
+            q.start[j] = start;
+            q.llr[j] = sg.llr;
+            q.frozen_words[j] = sg.code->d_frozen;
+            q.status[j] = sg.code->d_status;
+            q.u_hat[j] = sg.u_hat;
+            q.iters[j] = sg.iterations;
+            q.pe[j] = sg.pe_updates;
+            q.bitrev[j] = sg.code->bitrev;
+            start += sg.count;
+        }
+        q.start[q.nseg] = start;
+        q.total = start;
+    }
     return POLARBP_OK;
 }
 
@@ -724,44 +800,18 @@ int polarbp_get_codewords_per_block(const polarbp_code* c, int* cpc)
 int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
                             int freeze_mode, void* workspace, size_t workspace_bytes, void* stream)
 {
-    if (nseg < 0 || (nseg > 0 && !segs)) return fail(POLARBP_ERR_ARG, "bad segment list");
-    if (max_iter < 1) return fail(POLARBP_ERR_ARG, "max_iter must be >= 1");
-    if (!(scale > 0.f) || !std::isfinite(scale)) return fail(POLARBP_ERR_ARG, "scale must be finite and > 0");
-    if (stop_mode != POLARBP_STOP_NONE && stop_mode != POLARBP_STOP_GMATRIX)
-        return fail(POLARBP_ERR_ARG, "unknown stop_mode");
-    if (freeze_mode != POLARBP_FREEZE_OFF && freeze_mode != POLARBP_FREEZE_CSFG)
-        return fail(POLARBP_ERR_ARG, "unknown freeze_mode");
-    if (!workspace || workspace_bytes < (size_t)kSegWorkspace) return fail(POLARBP_ERR_ARG, "workspace too small");
-    std::vector<int> by_m[13];
-    for (int k = 0; k < nseg; ++k) {
-        const polarbp_segment& g = segs[k];
-        if (!g.code) return fail(POLARBP_ERR_ARG, "segment without a code");
-        if (g.code->m < 8 || g.code->m > 12)
-            return fail(POLARBP_ERR_UNSUPPORTED, "segments support N from 256 to 4096");
-        if (g.count < 0) return fail(POLARBP_ERR_ARG, "segment count must be >= 0");
-        if (g.count == 0) continue;
-        if (!g.llr || !g.u_hat) return fail(POLARBP_ERR_ARG, "segment llr and u_hat must be device pointers");
-        int rc = check_device(g.code);
-        if (rc != POLARBP_OK) return rc;
-        by_m[g.code->m].push_back(k);
-    }
+    polarbp::SegArgs args[13];
+    int rc = group_segments(segs, nseg, max_iter, scale, stop_mode, freeze_mode, workspace, workspace_bytes, true, args);
+    if (rc != POLARBP_OK) return rc;
     SideResources* side = nullptr;
-    int rc = side_resources(&side);
+    rc = side_resources(&side);
     if (rc != POLARBP_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(workspace, 0, kSegWorkspace, s);
     if (e != cudaSuccess) return cuda_fail(e, "segment counters");
     std::vector<int> ms;
-    for (int m = 8; m <= 12; ++m) {
-        if (by_m[m].empty()) continue;
-        if ((int)by_m[m].size() > polarbp::kMaxSeg) return fail(POLARBP_ERR_ARG, "at most 8 segments per code length");
-        long long total = 0;
-        for (int k : by_m[m]) total += segs[k].count;
-        if (total > 0x7fffffffLL) return fail(POLARBP_ERR_ARG, "too many codewords of one length");
-        const int cpc = segs[by_m[m][0]].code->cpc;
-        if (!polarbp::persistent_supported(m, cpc)) return fail(POLARBP_ERR_UNSUPPORTED, "codewords per block");
-        ms.push_back(m);
-    }
+    for (int m = 8; m <= 12; ++m)
+        if (args[m].total > 0) ms.push_back(m);
     if (ms.empty()) return POLARBP_OK;
     if (ms.size() > 1) {
         e = cudaEventRecord(side->fork, s);
@@ -771,28 +821,10 @@ int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter,
     for (size_t g = 0; g < ms.size(); ++g) {
         const int m = ms[g];
         polarbp::SegLaunch q{};
-        q.args.nseg = (int)by_m[m].size();
-        q.args.queue = static_cast<int*>(workspace) + m;
-        q.args.max_iter = max_iter;
-        q.args.alpha = scale;
-        int start = 0;
-        for (int j = 0; j < q.args.nseg; ++j) {
-            const polarbp_segment& sg = segs[by_m[m][j]];
-            q.args.start[j] = start;
-            q.args.llr[j] = sg.llr;
-            q.args.frozen_words[j] = sg.code->d_frozen;
-            q.args.status[j] = sg.code->d_status;
-            q.args.u_hat[j] = sg.u_hat;
-            q.args.iters[j] = sg.iterations;
-            q.args.pe[j] = sg.pe_updates;
-            q.args.bitrev[j] = sg.code->bitrev;
-            start += sg.count;
-        }
-        q.args.start[q.args.nseg] = start;
-        q.args.total = start;
+        q.args = args[m];
         q.stop_mode = stop_mode;
         q.freeze_mode = freeze_mode;
-        q.cpc = segs[by_m[m][0]].code->cpc;
+        q.cpc = segs[first_of_length(segs, nseg, m)].code->cpc;
         q.sms = side->sms;
         q.stream = g == 0 ? s : side->side[g - 1];
         e = launch_persistent_m(m, q);
@@ -803,6 +835,36 @@ int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter,
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side->join[g - 1], 0);
         if (e != cudaSuccess) return cuda_fail(e, "stream join");
     }
+    return POLARBP_OK;
+}
+
+int polarbp_decode_mixed(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
+                         int freeze_mode, void* workspace, size_t workspace_bytes, void* stream)
+{
+    polarbp::MixedArgs a{};
+    polarbp::SegArgs args[13];
+    int rc = group_segments(segs, nseg, max_iter, scale, stop_mode, freeze_mode, workspace, workspace_bytes, false, args);
+    if (rc != POLARBP_OK) return rc;
+    int top = 0;
+    for (int m = 8; m <= 12; ++m) {
+        a.seg[m - 8] = args[m];
+        if (args[m].total > 0) top = m;
+    }
+    SideResources* side = nullptr;
+    rc = side_resources(&side);
+    if (rc != POLARBP_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, kSegWorkspace, s);
+    if (e != cudaSuccess) return cuda_fail(e, "segment counters");
+    if (top == 0) return POLARBP_OK;
+    switch (top) {
+    case 8: e = polarbp::launch_mixed_m8(a, stop_mode, freeze_mode, side->sms, s); break;
+    case 9: e = polarbp::launch_mixed_m9(a, stop_mode, freeze_mode, side->sms, s); break;
+    case 10: e = polarbp::launch_mixed_m10(a, stop_mode, freeze_mode, side->sms, s); break;
+    case 11: e = polarbp::launch_mixed_m11(a, stop_mode, freeze_mode, side->sms, s); break;
+    default: e = polarbp::launch_mixed_m12(a, stop_mode, freeze_mode, side->sms, s); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mixed decode launch");
     return POLARBP_OK;
 }
 

@@ -82,3 +82,19 @@ def test_calls_on_a_null_handle_fail_cleanly(lib):
     assert lib.polarbp_code_info(None, None, None, None) == B.POLARBP_ERR_ARG
     assert lib.polarbp_get_status(None, None) == B.POLARBP_ERR_ARG
     lib.polarbp_destroy(None)
+
+
+@pytest.mark.parametrize("name", ["polarbp_decode_segments", "polarbp_decode_mixed"])
+def test_mixed_stream_entry_points_reject_bad_arguments_before_touching_cuda(lib, name):
+    f = getattr(lib, name)
+    ws = ctypes.c_void_p(16)  # never dereferenced: every call below fails its argument checks first
+    assert f(None, -1, 10, ctypes.c_float(0.9), 1, 1, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 1, 10, ctypes.c_float(0.9), 1, 1, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 0, ctypes.c_float(0.9), 1, 1, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 10, ctypes.c_float(0.0), 1, 1, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 10, ctypes.c_float(float("nan")), 1, 1, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 10, ctypes.c_float(0.9), 2, 1, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 10, ctypes.c_float(0.9), 1, 3, ws, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 10, ctypes.c_float(0.9), 1, 1, None, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
+    assert f(None, 0, 10, ctypes.c_float(0.9), 1, 1, ws, ctypes.c_size_t(4), None) == B.POLARBP_ERR_ARG
+    assert lib.polarbp_last_error().decode()
