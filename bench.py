@@ -463,7 +463,9 @@ def run_mixed(args):
     for k, (n_, k_) in enumerate(MIXED_CLASSES):
         members = idx[cls == k]
         code = B.polarbp_construct(n_, k_)
-        cpcs[f"{n_},{k_}"] = B.polarbp_autotune(code, MAX_ITER)
+        cpc = B.polarbp_autotune(code, MAX_ITER)
+        mapping = "pipelined" if B.polarbp_get_thread_mapping(code) == B.POLARBP_MAP_PIPELINED else "block"
+        cpcs[f"{n_},{k_}"] = {"codewords_per_block": cpc, "thread_mapping": mapping}
         ebn0 = torch.from_numpy(I.uniform(seed, members, 1.5, 3.5).astype(np.float32)).cuda()
         u, llr = B.polarbp_awgn_ebn0(code, seed, int(members[0]) if len(members) else 0, ebn0)
         n = len(members)
@@ -537,7 +539,7 @@ def run_mixed(args):
                                    + ("one persistent launch for all lengths (polarbp_decode_mixed)" if one_launch
                                       else "one persistent launch per length (polarbp_decode_segments)")
                                    + " in a CUDA graph, the faster of the two",
-                       "codewords_per_block": cpcs},
+                       "autotuned": cpcs},
             "variants_ms_per_step": {"one_launch_graph": ms_one, "one_launch_uncaptured": ms_one_unc,
                                      "per_length_graph": ms_per_len,
                                      "per_length_uncaptured": ms_persist,

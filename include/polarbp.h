@@ -52,6 +52,17 @@ typedef enum polarbp_freeze_mode {
     POLARBP_FREEZE_CSFG_MULTI = 2  /* a variant reading of Sec. III: checks continue along a stage */
 } polarbp_freeze_mode;
 
+/* How the threads of a block share one codeword's work when freezing
+ * (POLARBP_FREEZE_CSFG) at N = 256 .. 2048.  Decisions, iteration and PE counts
+ * are the same under both; only the schedule differs. */
+typedef enum polarbp_thread_mapping {
+    POLARBP_MAP_PIPELINED = 0,  /* N/8 sweep threads plus one checker warp that runs the CSFG
+                                   checks of iteration t while the sweep runs iteration t+1
+                                   (one codeword per block); the default */
+    POLARBP_MAP_BLOCK = 1       /* N/8 threads that sweep, then one of their warps checks while
+                                   the others wait (1, 2 or 4 codewords per block) */
+} polarbp_thread_mapping;
+
 /* Opaque code handle: the frozen set plus its device-side tables.  Owned by the
  * library; create with polarbp_construct, release with polarbp_destroy. */
 typedef struct polarbp_code polarbp_code;
@@ -382,10 +393,22 @@ int polarbp_decode_mixed(const polarbp_segment* segs, int nseg, int max_iter, fl
 int polarbp_set_codewords_per_block(polarbp_code* code, int codewords_per_block);
 int polarbp_get_codewords_per_block(const polarbp_code* code, int* codewords_per_block);
 
+/* polarbp_set_thread_mapping / polarbp_get_thread_mapping -- the thread mapping
+ * (polarbp_thread_mapping) that polarbp_decode, polarbp_decode_host and
+ * polarbp_decode_segments use for this code when freezing at N = 256 .. 2048.
+ * The pipelined mapping holds one codeword per block: with codewords per block
+ * above 1 the persistent launch takes the block mapping.  polarbp_decode_mixed
+ * always takes the block mapping.  Errors: POLARBP_ERR_ARG (NULL handle, unknown
+ * mapping). */
+int polarbp_set_thread_mapping(polarbp_code* code, int mapping);
+int polarbp_get_thread_mapping(const polarbp_code* code, int* mapping);
+
 /*
  * polarbp_autotune -- time the persistent decode of a synthetic batch
- * (BPSK/AWGN at 2.5 dB, about 8M LLRs) for every admissible codewords-per-block
- * value with the given decode settings and keep the fastest in the handle.
+ * (BPSK/AWGN at 2.5 dB, about 8M LLRs) for every admissible thread mapping and
+ * codewords-per-block value with the given decode settings (the pipelined
+ * mapping with one codeword per block, and the block mapping with 1, 2 or 4,
+ * as the code length admits) and keep the fastest pair in the handle.
  * Allocates and frees temporary device memory; synchronises `stream`.
  * Errors: POLARBP_ERR_ARG (K = 0), POLARBP_ERR_UNSUPPORTED, POLARBP_ERR_NOMEM, POLARBP_ERR_CUDA.
  */

@@ -28,6 +28,8 @@ POLARBP_STOP_GMATRIX = 1
 POLARBP_FREEZE_OFF = 0
 POLARBP_FREEZE_CSFG = 1
 POLARBP_FREEZE_CSFG_MULTI = 2
+POLARBP_MAP_PIPELINED = 0
+POLARBP_MAP_BLOCK = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -72,6 +74,8 @@ _SIGS = {
                                             ctypes.c_int, _VP, ctypes.c_size_t, _VP]),
     "polarbp_set_codewords_per_block": (ctypes.c_int, [_VP, ctypes.c_int]),
     "polarbp_get_codewords_per_block": (ctypes.c_int, [_VP, _VP]),
+    "polarbp_set_thread_mapping": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "polarbp_get_thread_mapping": (ctypes.c_int, [_VP, _VP]),
     "polarbp_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _VP]),
     "polarbp_wms_workspace": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
     "polarbp_wms_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t,
@@ -284,8 +288,21 @@ def polarbp_get_codewords_per_block(code: PolarCode) -> int:
     return v.value
 
 
+def polarbp_set_thread_mapping(code: PolarCode, mapping: int) -> None:
+    _check(lib().polarbp_set_thread_mapping(code.handle, mapping), "polarbp_set_thread_mapping")
+
+
+def polarbp_get_thread_mapping(code: PolarCode) -> int:
+    v = ctypes.c_int()
+    _check(lib().polarbp_get_thread_mapping(code.handle, ctypes.byref(v)), "polarbp_get_thread_mapping")
+    return v.value
+
+
 def polarbp_autotune(code: PolarCode, max_iter: int, scale: float = 0.9375, stop_mode: int = 1,
                      freeze_mode: int = 1, stream=None) -> int:
+    """Time every admissible (thread mapping, codewords per block) pair and keep the fastest
+    in the handle; returns the codewords per block (polarbp_get_thread_mapping gives the
+    mapping)."""
     _check(lib().polarbp_autotune(code.handle, max_iter, scale, stop_mode, freeze_mode, _stream(stream)),
            "polarbp_autotune")
     return polarbp_get_codewords_per_block(code)

@@ -1478,6 +1478,7 @@ struct LaunchReq {
     int stop_mode;
     int freeze_mode;
     bool trace;
+    bool pipelined = true;  // freezing at N = 256 .. 2048: the checker-warp mapping (bp_pipe.cuh)
     cudaStream_t stream;
 };
 
@@ -1523,6 +1524,7 @@ struct SegLaunch {
     int stop_mode;
     int freeze_mode;
     int cpc;
+    bool pipelined = true;  // freezing at N = 256 .. 2048 with cpc 1: the checker-warp mapping (bp_pipe.cuh)
     int sms;
     cudaStream_t stream;
 };

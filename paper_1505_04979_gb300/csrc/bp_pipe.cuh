@@ -411,18 +411,18 @@ __device__ __forceinline__ bool sweep_pipe(Regs<M>& rg, Smem<M>& sm, int tid, fl
     }
 }
 
-// One codeword per block: Geo<M>::BLOCK workers and one checker warp.
+// Decode one codeword with the whole block (Geo<M>::BLOCK workers and one
+// checker warp) on the block's shared memory smem_raw.  Every named barrier the
+// call uses is complete when it returns, so a block may decode codewords back
+// to back (after a block barrier).
 template <int M, bool GSTOP>
-__global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) bp_decode_pipe_kernel(DecodeArgs args)
+__device__ __forceinline__ void decode_pipe_codeword(const CwIO& a, int max_iter, float alpha, unsigned int* status,
+                                                     unsigned char* smem_raw)
 {
     using G = Geo<M>;
     constexpr int N = G::N, EL = G::EL, T = G::T, NW = G::NW, NP = G::NP;
     constexpr int WORKERS = PipeGeo<M>::WORKERS, THREADS = PipeGeo<M>::THREADS;
     static_assert(natural_rows<M>() && T == WORKERS, "codes of N >= 256");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const long long cw = blockIdx.x;
-    const CwIO a{args.llr + cw * N, args.frozen_words, args.u_hat + cw * N, args.iters ? args.iters + cw : nullptr,
-                 args.pe ? args.pe + cw : nullptr, nullptr, nullptr, nullptr, args.bitrev};
     const int tid = threadIdx.x;
     Smem<M> sm(smem_raw);
 
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
         sm.ctl[CTL_Q] = 1;
         *sm.pe_acc() = 0;
     }
-    if (!stage_llr<M>(sm.llr, a.llr, tid, THREADS, a.bitrev)) atomicOr(args.status, 1u);
+    if (!stage_llr<M>(sm.llr, a.llr, tid, THREADS, a.bitrev)) atomicOr(status, 1u);
     __syncthreads();
 
     if (tid < WORKERS) {
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
             pipe_buffers<M>(sm, smem_raw, it);
 #pragma unroll
             for (int e = 0; e < EL; ++e) rg.R[e] = sm.llr[e * T + tid];
-            if (!sweep_pipe<M, 0, GSTOP>(rg, sm, tid, args.alpha, a)) break;
+            if (!sweep_pipe<M, 0, GSTOP>(rg, sm, tid, alpha, a)) break;
             __threadfence_block();
             bar_arrive(kBarSwept, THREADS);
         }
@@ -475,12 +475,12 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
             pipe_buffers<M>(sm, smem_raw, t);
             if (lane == 0) {
                 sm.ctl[CTL_EVENT] = 0;
-                if (t >= args.max_iter) sm.ctl[CTL_DONE] = 1;  // the iteration cap: no further sweep
+                if (t >= max_iter) sm.ctl[CTL_DONE] = 1;  // the iteration cap: no further sweep
             }
             __syncwarp();
             int released = 0;
             pe += walk_pipe<M>(sm, ss, P, lane, released);
-            bool done = (P >= N) || t >= args.max_iter;
+            bool done = (P >= N) || t >= max_iter;
             if constexpr (GSTOP) {
                 if (!done) done = gmatrix_ok_pre<M>(sm, P, lane);
             }
@@ -517,6 +517,50 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
     }
 }
 
+// One codeword per block.
+template <int M, bool GSTOP>
+__global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) bp_decode_pipe_kernel(DecodeArgs args)
+{
+    constexpr int N = Geo<M>::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const long long cw = blockIdx.x;
+    const CwIO a{args.llr + cw * N, args.frozen_words, args.u_hat + cw * N, args.iters ? args.iters + cw : nullptr,
+                 args.pe ? args.pe + cw : nullptr, nullptr, nullptr, nullptr, args.bitrev};
+    decode_pipe_codeword<M, GSTOP>(a, args.max_iter, args.alpha, args.status, smem_raw);
+}
+
+// Persistent form: each block takes the next codeword from the device counter,
+// decodes it pipelined and retires it at its own stop, until the queue is empty.
+template <int M, bool GSTOP>
+__global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) bp_decode_pipe_persistent(SegArgs a)
+{
+    constexpr int N = Geo<M>::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<M> sm(smem_raw);
+    int* qslot = sm.ctl + CTL_Q;
+    for (;;) {
+        __syncthreads();  // the previous codeword's readers are done with shared memory
+        if (threadIdx.x == 0) *qslot = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = *qslot;
+        if (q >= a.total) break;
+        int sg = 0;
+        while (sg + 1 < a.nseg && q >= a.start[sg + 1]) ++sg;
+        const long long r = q - a.start[sg];
+        const CwIO io{a.llr[sg] + r * N,
+                      a.frozen_words[sg],
+                      a.u_hat[sg] + r * N,
+                      a.iters[sg] ? a.iters[sg] + r : nullptr,
+                      a.pe[sg] ? a.pe[sg] + r : nullptr,
+                      nullptr,
+                      nullptr,
+                      nullptr,
+                      a.bitrev[sg]};
+        __syncthreads();  // every thread has read the popped index before the decode reuses the slot
+        decode_pipe_codeword<M, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
+    }
+}
+
 template <int M, bool GSTOP>
 cudaError_t launch_pipe(const DecodeArgs& args, cudaStream_t stream)
 {
@@ -531,16 +575,61 @@ cudaError_t launch_pipe(const DecodeArgs& args, cudaStream_t stream)
 }
 
 // Decode launches of one code length: G-stop + freezing and freezing alone
-// (reading A, without message planes) run pipelined for N = 256 .. 2048, the rest
-// on bp_decode_kernel.
+// (reading A, without message planes) run pipelined for N = 256 .. 2048 unless
+// the code asks for the one-block mapping, the rest on bp_decode_kernel.
 template <int M>
 cudaError_t launch_decode_pipe(const LaunchReq& q)
 {
     if constexpr (M >= 8 && M <= 11) {
-        if (q.freeze_mode == 1 && !q.trace)
+        if (q.freeze_mode == 1 && !q.trace && q.pipelined)
             return q.stop_mode ? launch_pipe<M, true>(q.args, q.stream) : launch_pipe<M, false>(q.args, q.stream);
     }
     return launch_decode<M>(q);
+}
+
+template <int M, bool GSTOP>
+cudaError_t launch_pipe_persistent(const SegLaunch& q)
+{
+    auto kern = bp_decode_pipe_persistent<M, GSTOP>;
+    constexpr size_t smem = PipeLayout<M>::bytes;
+    constexpr int threads = PipeGeo<M>::THREADS;
+    // blocks per SM, per device, set with the shared-memory attribute on the device's first launch
+    constexpr int kDevices = 64;
+    static std::atomic<int> blocks_per_sm[kDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+    int bps = blocks_per_sm[dev].load(std::memory_order_acquire);
+    if (bps == 0) {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        bps = b > 0 ? b : 1;
+        blocks_per_sm[dev].store(bps, std::memory_order_release);
+    }
+    long long grid = (long long)bps * q.sms;
+    if (grid > q.args.total) grid = q.args.total;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, threads, smem, q.stream>>>(q.args);
+    return cudaGetLastError();
+}
+
+// Persistent launches of one code length: the pipelined mapping for freezing
+// (reading A) at N = 256 .. 2048 with one codeword per block, unless the code
+// asks for the one-block mapping; otherwise bp_decode_persistent.
+template <int M>
+cudaError_t launch_persistent_pipe(const SegLaunch& q)
+{
+    if constexpr (M >= 8 && M <= 11) {
+        if (q.freeze_mode == 1 && q.pipelined && q.cpc == 1)
+            return q.stop_mode ? launch_pipe_persistent<M, true>(q) : launch_pipe_persistent<M, false>(q);
+    }
+    return launch_persistent<M>(q);
 }
 
 }  // namespace polarbp

@@ -25,6 +25,7 @@ struct polarbp_code {
     uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
     unsigned int* d_status = nullptr;
     int cpc = 1;  // codewords per block of the persistent launch
+    int mapping = POLARBP_MAP_PIPELINED;  // thread mapping when freezing at N = 256 .. 2048
     int bitrev = 0;  // 1: channel position i carries code position rev(i) (Arikan's B_N)
     // polarbp_decode_host's pipeline, created with the handle so that the call
     // itself creates nothing; `pipe_lock` serialises enqueueing on them
@@ -287,6 +288,7 @@ int decode_impl(const polarbp_code* c, const float* llr, int batch, int max_iter
     q.stop_mode = stop_mode;
     q.freeze_mode = freeze_mode;
     q.trace = trace;
+    q.pipelined = c->mapping == POLARBP_MAP_PIPELINED;
     q.stream = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     switch (c->m) {
@@ -797,6 +799,22 @@ int polarbp_get_codewords_per_block(const polarbp_code* c, int* cpc)
     return POLARBP_OK;
 }
 
+int polarbp_set_thread_mapping(polarbp_code* c, int mapping)
+{
+    if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
+    if (mapping != POLARBP_MAP_PIPELINED && mapping != POLARBP_MAP_BLOCK)
+        return fail(POLARBP_ERR_ARG, "unknown thread mapping");
+    c->mapping = mapping;
+    return POLARBP_OK;
+}
+
+int polarbp_get_thread_mapping(const polarbp_code* c, int* mapping)
+{
+    if (!c || !mapping) return fail(POLARBP_ERR_ARG, "NULL argument");
+    *mapping = c->mapping;
+    return POLARBP_OK;
+}
+
 int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter, float scale, int stop_mode,
                             int freeze_mode, void* workspace, size_t workspace_bytes, void* stream)
 {
@@ -824,7 +842,9 @@ int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter,
         q.args = args[m];
         q.stop_mode = stop_mode;
         q.freeze_mode = freeze_mode;
-        q.cpc = segs[first_of_length(segs, nseg, m)].code->cpc;
+        const polarbp_code* c0 = segs[first_of_length(segs, nseg, m)].code;
+        q.cpc = c0->cpc;
+        q.pipelined = c0->mapping == POLARBP_MAP_PIPELINED;
         q.sms = side->sms;
         q.stream = g == 0 ? s : side->side[g - 1];
         e = launch_persistent_m(m, q);
@@ -888,14 +908,22 @@ int polarbp_autotune(polarbp_code* c, int max_iter, float scale, int stop_mode, 
     int rc = POLARBP_OK;
     if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? fail(POLARBP_ERR_NOMEM, "autotune buffers")
                                                                  : cuda_fail(e, "autotune setup");
-    const int keep = c->cpc;
-    int best = keep;
+    const int keep = c->cpc, keep_map = c->mapping;
+    int best = keep, best_map = keep_map;
     float best_ms = 3.4e38f;
     if (rc == POLARBP_OK) rc = polarbp_awgn(c, 1, 0, B, 2.5f, nullptr, d_llr, stream);
-    for (int cpc : {1, 2, 4}) {
+    // candidates (mapping, codewords per block); the pipelined mapping exists for freezing
+    // (reading A) at N = 256 .. 2048 with one codeword per block
+    const bool pipe_ok = freeze_mode == POLARBP_FREEZE_CSFG && c->m <= 11;
+    const std::pair<int, int> cands[] = {{POLARBP_MAP_PIPELINED, 1}, {POLARBP_MAP_BLOCK, 1}, {POLARBP_MAP_BLOCK, 2},
+                                         {POLARBP_MAP_BLOCK, 4}};
+    for (const auto& cand : cands) {
+        const int map = cand.first, cpc = cand.second;
         if (rc != POLARBP_OK) break;
+        if (map == POLARBP_MAP_PIPELINED && !pipe_ok) continue;
         if (!polarbp::persistent_supported(c->m, cpc)) continue;
         c->cpc = cpc;
+        c->mapping = map;
         polarbp_segment sg{c, d_llr, d_u, nullptr, nullptr, B};
         rc = polarbp_decode_segments(&sg, 1, max_iter, scale, stop_mode, freeze_mode, ws, kSegWorkspace, stream);
         if (rc != POLARBP_OK) break;
@@ -916,9 +944,11 @@ int polarbp_autotune(polarbp_code* c, int max_iter, float scale, int stop_mode, 
         if (ms < best_ms) {
             best_ms = ms;
             best = cpc;
+            best_map = map;
         }
     }
     c->cpc = rc == POLARBP_OK ? best : keep;
+    c->mapping = rc == POLARBP_OK ? best_map : keep_map;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(d_llr);

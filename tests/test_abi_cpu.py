@@ -98,3 +98,9 @@ def test_mixed_stream_entry_points_reject_bad_arguments_before_touching_cuda(lib
     assert f(None, 0, 10, ctypes.c_float(0.9), 1, 1, None, ctypes.c_size_t(256), None) == B.POLARBP_ERR_ARG
     assert f(None, 0, 10, ctypes.c_float(0.9), 1, 1, ws, ctypes.c_size_t(4), None) == B.POLARBP_ERR_ARG
     assert lib.polarbp_last_error().decode()
+
+
+def test_thread_mapping_calls_reject_bad_arguments(lib):
+    v = ctypes.c_int()
+    assert lib.polarbp_set_thread_mapping(None, B.POLARBP_MAP_BLOCK) == B.POLARBP_ERR_ARG
+    assert lib.polarbp_get_thread_mapping(None, ctypes.byref(v)) == B.POLARBP_ERR_ARG

@@ -101,6 +101,20 @@ def test_decode_matches_binary32_oracle(B, N, mode):
         assert np.array_equal(uh, ouh)
 
 
+@pytest.mark.parametrize("N", [256, 512, 1024, 2048])
+@pytest.mark.parametrize("mode", [(1, 1), (0, 1)])
+def test_block_mapping_matches_binary32_oracle(B, N, mode):
+    """Freezing at N = 256 .. 2048 under the block thread mapping (the sweep warps take turns
+    with the checks) instead of the default pipelined one: the same bits and counts."""
+    K = N // 2
+    code = B.polarbp_construct(N, K)
+    B.polarbp_set_thread_mapping(code, B.POLARBP_MAP_BLOCK)
+    fz, u, x, llr = host_inputs(N, K, 64, 2.5, 3000 + N)
+    uh, it, pe = gpu_decode(B, code, llr, 40, *mode)
+    ouh, oit, ope, _ = O.decode_batch(fz, llr, 40, ALPHA, mode[0], mode[1], fp32=True)
+    assert np.array_equal(it, oit) and np.array_equal(pe, ope) and np.array_equal(uh, ouh)
+
+
 @pytest.mark.parametrize("N", [8, 16, 64, 128, 512, 1024, 4096])
 @pytest.mark.parametrize("mode", MODES + MODES_B)
 def test_message_planes_match_binary32_oracle(B, N, mode):

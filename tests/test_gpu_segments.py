@@ -53,13 +53,18 @@ def run_segments(B, codes, llrs, max_iter, mode, entry="polarbp_decode_segments"
 
 
 @pytest.mark.parametrize("mode", [(1, 1), (1, 0), (0, 1), (0, 0)])
-@pytest.mark.parametrize("cpc", [1, 2, 4])
-def test_mixed_segments_match_binary32_oracle(B, mode, cpc):
+@pytest.mark.parametrize("mapping,cpc", [(0, 1), (1, 1), (1, 2), (1, 4)])
+def test_mixed_segments_match_binary32_oracle(B, mode, mapping, cpc):
+    """Per-length persistent launches under every (thread mapping, codewords per block) pair:
+    the pipelined mapping (checker warp beside the sweep) with one codeword per block, the
+    block mapping with 1, 2 or 4."""
     counts = [40, 40, 40, 24, 24, 24, 6, 6, 6]
     codes, llrs, fzs = [], [], []
     first = 0
     for (N, K), n in zip(CLASSES, counts):
         code = B.polarbp_construct(N, K)
+        B.polarbp_set_thread_mapping(code, mapping)
+        assert B.polarbp_get_thread_mapping(code) == mapping
         try:
             B.polarbp_set_codewords_per_block(code, cpc)
         except B.PolarBPError:
@@ -100,11 +105,24 @@ def test_segments_graph_capture_and_replay(B):
 
 
 @pytest.mark.parametrize("N", [256, 1024, 4096])
-def test_autotune_picks_an_admissible_value(B, N):
+@pytest.mark.parametrize("freeze", [0, 1])
+def test_autotune_picks_an_admissible_pair(B, N, freeze):
     code = B.polarbp_construct(N, N // 2)
-    cpc = B.polarbp_autotune(code, 40)
-    assert cpc in (1, 2, 4)
+    cpc = B.polarbp_autotune(code, 40, freeze_mode=freeze)
+    mapping = B.polarbp_get_thread_mapping(code)
+    assert cpc in (1, 2, 4) and mapping in (B.POLARBP_MAP_PIPELINED, B.POLARBP_MAP_BLOCK)
+    if mapping == B.POLARBP_MAP_PIPELINED and freeze == 1 and N <= 2048:
+        assert cpc == 1  # the pipelined mapping holds one codeword per block
     B.polarbp_set_codewords_per_block(code, cpc)
+
+
+def test_thread_mapping_rejects_unknown_values(B):
+    code = B.polarbp_construct(1024, 512)
+    assert B.polarbp_get_thread_mapping(code) == B.POLARBP_MAP_PIPELINED  # the default
+    with pytest.raises(B.PolarBPError) as e:
+        B.polarbp_set_thread_mapping(code, 2)
+    assert e.value.code == B.POLARBP_ERR_ARG
+    assert B.polarbp_get_thread_mapping(code) == B.POLARBP_MAP_PIPELINED
 
 
 @pytest.mark.parametrize("entry", ["polarbp_decode_segments", "polarbp_decode_mixed"])
