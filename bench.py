@@ -976,7 +976,8 @@ def run_wms(args):
         info = torch.from_numpy(np.nonzero(code.frozen_mask() == 0)[0]).cuda()
         w = torch.full((T, m, N // 2), ALPHA, dtype=torch.float32, device="cuda", requires_grad=True)
         opt = torch.optim.Adam([w], lr=args.wms_lr)
-        ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
+        kk = args.wms_k
+        ws = torch.empty(B.polarbp_wms_workspace(code, batch, T, kk), dtype=torch.uint8, device="cuda")
         losses, fwd_ms, bwd_ms = [], 0.0, 0.0
         e0, e1, e1b, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         for step in range(args.wms_steps):
@@ -986,7 +987,7 @@ def run_wms(args):
             target = u[:, info].float()
             opt.zero_grad()
             e0.record(stream)
-            out = B.polarbp_wms_forward(code, llr, w.detach(), ws)
+            out = B.polarbp_wms_forward(code, llr, w.detach(), ws, checkpoint_every=kk)
             e1.record(stream)
             x = (-out[:, info]).detach().requires_grad_(True)
             loss = torch.nn.functional.binary_cross_entropy_with_logits(x, target)
@@ -994,7 +995,7 @@ def run_wms(args):
             dout = torch.zeros((batch, N), dtype=torch.float32, device="cuda")
             dout[:, info] = -x.grad
             e1b.record(stream)
-            dw, _ = B.polarbp_wms_backward(code, llr, w.detach(), dout, ws)
+            dw, _ = B.polarbp_wms_backward(code, llr, w.detach(), dout, ws, checkpoint_every=kk)
             e2.record(stream)
             w.grad = dw
             opt.step()
@@ -1006,9 +1007,34 @@ def run_wms(args):
         timed = max(1, args.wms_steps - 3)
         fwd_ms /= timed
         bwd_ms /= timed
-        plane = (m + 1) * N * 4
-        fwd_bytes = batch * (4 * N + 4 * N + 2 * T * plane)
-        bwd_bytes = batch * (2 * T * plane + 4 * N * 3 + T * m * (N // 2) * 4)
+        def wms_bytes(k):
+            """Algorithmic bytes per batch: LLRs in and soft outputs out, the checkpoints (both
+            planes of every iteration for k = 1, L columns 1..m-1 after every k-th iteration
+            otherwise) written by the forward and read by the adjoint, dout in, dllr out and the
+            per-codeword weight-gradient partials out."""
+            ck = T * 2 * (m + 1) * N * 4 if k == 1 else ((T - 1) // min(k, T)) * (m - 1) * N * 4
+            return batch * (4 * N + 4 * N + ck), batch * (ck + 4 * N * 3 + T * m * (N // 2) * 4)
+
+        fwd_bytes, bwd_bytes = wms_bytes(kk)
+        # forward and adjoint times against the checkpoint interval, on the last training batch
+        ksweep = {}
+        for k in (1, 2, 5, 10):
+            wsk = torch.empty(B.polarbp_wms_workspace(code, batch, T, k), dtype=torch.uint8, device="cuda")
+            fb, bb = wms_bytes(k)
+            tf = tb = 0.0
+            for rep in range(5):
+                e0.record(stream)
+                B.polarbp_wms_forward(code, llr, w.detach(), wsk, checkpoint_every=k)
+                e1.record(stream)
+                B.polarbp_wms_backward(code, llr, w.detach(), dout, wsk, checkpoint_every=k)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                if rep >= 2:
+                    tf += e0.elapsed_time(e1) / 3
+                    tb += e1.elapsed_time(e2) / 3
+            ksweep[f"k={k}"] = {"forward_ms": tf, "backward_ms": tb, "workspace_bytes": wsk.numel(),
+                                "forward_hbm_frac": fb / (tf * 1e-3) / hbm, "backward_hbm_frac": bb / (tb * 1e-3) / hbm}
+            del wsk
         fer = {}
         with torch.no_grad():
             for eb in (2.0, 3.0, 4.0):
@@ -1018,7 +1044,7 @@ def run_wms(args):
                     first = (1 << 30) + chunk * batch
                     u, llr = B.polarbp_awgn(code, SEED + 6, first, batch, eb)
                     for weights, key in ((w.detach(), "learned"), (wc, "constant")):
-                        out = B.polarbp_wms_forward(code, llr, weights, ws)
+                        out = B.polarbp_wms_forward(code, llr, weights, ws, checkpoint_every=kk)
                         uh = (out[:, info] < 0).to(torch.uint8)
                         e = int((uh != u[:, info]).any(dim=1).sum().item())
                         if key == "learned":
@@ -1036,7 +1062,7 @@ def run_wms(args):
             "train_codewords_per_s": batch / ((fwd_ms + bwd_ms) * 1e-3),
             "forward_GBps": fwd_bytes / (fwd_ms * 1e-3) / 1e9, "backward_GBps": bwd_bytes / (bwd_ms * 1e-3) / 1e9,
             "forward_hbm_frac": fwd_bytes / (fwd_ms * 1e-3) / hbm, "backward_hbm_frac": bwd_bytes / (bwd_ms * 1e-3) / hbm,
-            "fer": fer}
+            "checkpoint_every": kk, "checkpoint_sweep": ksweep, "fer": fer}
     line = {"metric": "weighted min-sum training: codewords/s (forward + adjoint), FER learned vs constant",
             "value": results["N=256"]["train_codewords_per_s"], "unit": "codewords/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -1096,6 +1122,7 @@ def main():
     ap.add_argument("--long-ebn0", type=float, default=None, help="one Eb/N0 point of the long workload")
     ap.add_argument("--wms-steps", type=int, default=300)
     ap.add_argument("--wms-lr", type=float, default=0.005)
+    ap.add_argument("--wms-k", type=int, default=1, help="checkpoint interval of the weighted min-sum training")
     ap.add_argument("--wms-eval", type=int, default=1 << 17)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -431,14 +431,25 @@ int polarbp_awgn_ebn0(const polarbp_code* code, uint64_t seed, uint64_t first_co
  *   weights   device [iterations][m][N/2] float, weight (t, s, p) at (t m + s) N/2 + p.
  *   out       device [batch][N] soft outputs R[m] + L[m] after the last
  *             iteration (+inf on frozen positions: the prior).
- *   workspace device buffer of polarbp_wms_workspace(code, batch, iterations)
- *             bytes: the forward writes its per-iteration checkpoints there and
- *             the backward of the same batch reads them; keep it unchanged
+ *   checkpoint_every  k >= 1.  k = 1: the forward stores both message planes
+ *             after every iteration and the backward reads them back.  k > 1:
+ *             the forward stores only the state one iteration hands to the next
+ *             (L columns 1..m-1) after iterations k-1, 2k-1, ...; the backward
+ *             recomputes the iterations in between in shared memory with the
+ *             forward's arithmetic.  The results do not depend on k; k trades
+ *             workspace for recomputation.  k above `iterations` acts as
+ *             `iterations`.  With k > 1 the backward holds 3 + 2k message planes
+ *             of (m+1) N floats per block: k up to 26 at N = 128, 11 at N = 256,
+ *             4 at N = 512, 1 at N = 1024 (POLARBP_ERR_UNSUPPORTED beyond).  The
+ *             forward and the backward of one batch take the same k.
+ *   workspace device buffer of polarbp_wms_workspace(code, batch, iterations,
+ *             checkpoint_every) bytes: the forward writes its checkpoints there
+ *             and the backward of the same batch reads them; keep it unchanged
  *             between the two.
  */
-size_t polarbp_wms_workspace(const polarbp_code* code, int batch, int iterations);
-int polarbp_wms_forward(const polarbp_code* code, const float* llr, int batch, int iterations, const float* weights,
-                        float* out, void* workspace, size_t workspace_bytes, void* stream);
+size_t polarbp_wms_workspace(const polarbp_code* code, int batch, int iterations, int checkpoint_every);
+int polarbp_wms_forward(const polarbp_code* code, const float* llr, int batch, int iterations, int checkpoint_every,
+                        const float* weights, float* out, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * polarbp_wms_backward -- gradients of a loss through polarbp_wms_forward.
@@ -449,9 +460,9 @@ int polarbp_wms_forward(const polarbp_code* code, const float* llr, int batch, i
  * min is differentiated towards its smaller argument (ties: the first), sign
  * as a constant; +-inf messages (built from the frozen prior) are constants.
  */
-int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, int iterations, const float* weights,
-                         const float* dout, float* dweights, float* dllr, void* workspace, size_t workspace_bytes,
-                         void* stream);
+int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, int iterations, int checkpoint_every,
+                         const float* weights, const float* dout, float* dweights, float* dllr, void* workspace,
+                         size_t workspace_bytes, void* stream);
 
 /*
  * polarbp_get_status -- read and clear the handle's device status word.  Waits

@@ -77,11 +77,11 @@ _SIGS = {
     "polarbp_set_thread_mapping": (ctypes.c_int, [_VP, ctypes.c_int]),
     "polarbp_get_thread_mapping": (ctypes.c_int, [_VP, _VP]),
     "polarbp_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _VP]),
-    "polarbp_wms_workspace": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
-    "polarbp_wms_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t,
-                                           _VP]),
-    "polarbp_wms_backward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP,
-                                            ctypes.c_size_t, _VP]),
+    "polarbp_wms_workspace": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "polarbp_wms_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP,
+                                           ctypes.c_size_t, _VP]),
+    "polarbp_wms_backward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP,
+                                            _VP, ctypes.c_size_t, _VP]),
     "polarbp_get_status": (ctypes.c_int, [_VP, _VP]),
     "polarbp_last_error": (ctypes.c_char_p, []),
     "polarbp_version": (ctypes.c_char_p, []),
@@ -438,11 +438,11 @@ def polarbp_get_status(code: PolarCode, stream=None) -> int:
     return rc
 
 
-def polarbp_wms_workspace(code: PolarCode, batch: int, iterations: int) -> int:
-    return int(lib().polarbp_wms_workspace(code.handle, batch, iterations))
+def polarbp_wms_workspace(code: PolarCode, batch: int, iterations: int, checkpoint_every: int = 1) -> int:
+    return int(lib().polarbp_wms_workspace(code.handle, batch, iterations, checkpoint_every))
 
 
-def polarbp_wms_forward(code: PolarCode, llr, weights, workspace, out=None, stream=None):
+def polarbp_wms_forward(code: PolarCode, llr, weights, workspace, out=None, stream=None, checkpoint_every: int = 1):
     import torch
     B = llr.shape[0]
     T = weights.shape[0]
@@ -450,12 +450,12 @@ def polarbp_wms_forward(code: PolarCode, llr, weights, workspace, out=None, stre
     _need(weights, torch.float32, (T, code.m, code.N // 2), "weights")
     if out is None:
         out = torch.empty((B, code.N), dtype=torch.float32, device=llr.device)
-    _check(lib().polarbp_wms_forward(code.handle, _ptr(llr), B, T, _ptr(weights), _ptr(out), _ptr(workspace),
-                                     workspace.numel(), _stream(stream)), "polarbp_wms_forward")
+    _check(lib().polarbp_wms_forward(code.handle, _ptr(llr), B, T, checkpoint_every, _ptr(weights), _ptr(out),
+                                     _ptr(workspace), workspace.numel(), _stream(stream)), "polarbp_wms_forward")
     return out
 
 
-def polarbp_wms_backward(code: PolarCode, llr, weights, dout, workspace, stream=None):
+def polarbp_wms_backward(code: PolarCode, llr, weights, dout, workspace, stream=None, checkpoint_every: int = 1):
     import torch
     B = llr.shape[0]
     T = weights.shape[0]
@@ -463,14 +463,17 @@ def polarbp_wms_backward(code: PolarCode, llr, weights, dout, workspace, stream=
     _need(dout, torch.float32, (B, code.N), "dout")
     dw = torch.empty_like(weights)
     dl = torch.empty_like(llr)
-    _check(lib().polarbp_wms_backward(code.handle, _ptr(llr), B, T, _ptr(weights), _ptr(dout), _ptr(dw), _ptr(dl),
-                                      _ptr(workspace), workspace.numel(), _stream(stream)), "polarbp_wms_backward")
+    _check(lib().polarbp_wms_backward(code.handle, _ptr(llr), B, T, checkpoint_every, _ptr(weights), _ptr(dout),
+                                      _ptr(dw), _ptr(dl), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "polarbp_wms_backward")
     return dw, dl
 
 
-def weighted_min_sum(code: PolarCode, llr, weights):
+def weighted_min_sum(code: PolarCode, llr, weights, checkpoint_every: int = 1):
     """Differentiable weighted min-sum decoder: soft outputs [batch, N] as a function of
-    (llr, weights); gradients come from the library's adjoint kernel."""
+    (llr, weights); gradients come from the library's adjoint kernel.  ``checkpoint_every``:
+    the forward keeps the message state of every k-th iteration, the adjoint recomputes
+    the rest (the gradients do not depend on k)."""
     import torch
 
     class _WMS(torch.autograd.Function):
@@ -478,16 +481,17 @@ def weighted_min_sum(code: PolarCode, llr, weights):
         def forward(ctx, llr_t, w_t):
             llr_c = llr_t.detach().contiguous()
             w_c = w_t.detach().contiguous()
-            ws = torch.empty(polarbp_wms_workspace(code, llr_c.shape[0], w_c.shape[0]), dtype=torch.uint8,
-                             device=llr_c.device)
-            out = polarbp_wms_forward(code, llr_c, w_c, ws)
+            ws = torch.empty(polarbp_wms_workspace(code, llr_c.shape[0], w_c.shape[0], checkpoint_every),
+                             dtype=torch.uint8, device=llr_c.device)
+            out = polarbp_wms_forward(code, llr_c, w_c, ws, checkpoint_every=checkpoint_every)
             ctx.save_for_backward(llr_c, w_c, ws)
             return out
 
         @staticmethod
         def backward(ctx, dout):
             llr_c, w_c, ws = ctx.saved_tensors
-            dw, dl = polarbp_wms_backward(code, llr_c, w_c, dout.to(torch.float32), ws)
+            dw, dl = polarbp_wms_backward(code, llr_c, w_c, dout.to(torch.float32), ws,
+                                          checkpoint_every=checkpoint_every)
             return dl, dw
 
     return _WMS.apply(llr, weights)

@@ -34,22 +34,47 @@ def inputs(N, T, batch, seed, lo=1.0, hi=4.0):
     return fz, u, llr, w
 
 
+def checkpoints(ws, batch, T, k, m, N):
+    """The forward's checkpoints in the workspace.  k = 1: [batch][T][2][m+1][N], the L and R
+    planes after every iteration.  k > 1: [batch][(T-1)//k][m-1][N], checkpoint j = L columns
+    1..m-1 after iteration (j+1) k - 1."""
+    if k == 1:
+        return ws[: batch * T * 2 * (m + 1) * N * 4].view(torch.float32).view(batch, T, 2, m + 1, N)
+    nc = (T - 1) // k
+    return ws[: batch * nc * (m - 1) * N * 4].view(torch.float32).view(batch, nc, m - 1, N)
+
+
 @pytest.mark.parametrize("N", [2, 8, 16, 128, 256, 1024])
-def test_forward_planes_match_binary32_oracle(B, N):
+@pytest.mark.parametrize("k", [1, 3])
+def test_forward_state_matches_binary32_oracle(B, N, k):
+    """The soft outputs and the checkpoints (both planes after every iteration for k = 1, L
+    columns 1..m-1 after every k-th iteration otherwise) are bit-exact against the oracle's
+    binary32 forward."""
     T = 10
     m = N.bit_length() - 1
     batch = 6
     fz, u, llr, w = inputs(N, T, batch, N)
     code = B.polarbp_construct(N, N // 2)
-    ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
-    out = B.polarbp_wms_forward(code, torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(), ws)
+    if N == 1024 and k > 1:  # 3 + 2k planes of 45 KB
+        with pytest.raises(B.PolarBPError) as e:
+            B.polarbp_wms_forward(code, torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                  torch.empty(B.polarbp_wms_workspace(code, batch, T, k), dtype=torch.uint8,
+                                              device="cuda"), checkpoint_every=k)
+        assert e.value.code == B.POLARBP_ERR_UNSUPPORTED  # the adjoint's planes exceed shared memory
+        return
+    ws = torch.empty(B.polarbp_wms_workspace(code, batch, T, k), dtype=torch.uint8, device="cuda")
+    out = B.polarbp_wms_forward(code, torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(), ws,
+                                checkpoint_every=k)
     torch.cuda.synchronize()
-    ck = ws[: batch * T * 2 * (m + 1) * N * 4].view(torch.float32).view(batch, T, 2, m + 1, N).cpu().numpy()
+    ck = checkpoints(ws, batch, T, k, m, N).cpu().numpy()
     out = out.cpu().numpy()
     for c in range(batch):
         o, tl, tr = O.wms_forward(fz, llr[c], w.astype(np.float64), fp32=True, trace=True)
-        assert np.array_equal(ck[c, :, 0].astype(np.float64), tl)
-        assert np.array_equal(ck[c, :, 1].astype(np.float64), tr)
+        if k == 1:
+            assert np.array_equal(ck[c, :, 0].astype(np.float64), tl)
+            assert np.array_equal(ck[c, :, 1].astype(np.float64), tr)
+        for j in range((T - 1) // k if k > 1 else 0):
+            assert np.array_equal(ck[c, j].astype(np.float64), tl[(j + 1) * k - 1][1:m])
         assert np.array_equal(out[c].astype(np.float64), o)
 
 
@@ -61,11 +86,12 @@ def test_constant_weights_match_the_decoder(B):
     w = torch.full((T, m, N // 2), 0.9375, dtype=torch.float32, device="cuda")
     d = torch.from_numpy(llr).cuda()
     ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
-    B.polarbp_wms_forward(code, d, w, ws)
+    out = B.polarbp_wms_forward(code, d, w, ws)
     _, _, _, tL, tR, _ = B.polarbp_decode_trace(code, d, T, 0.9375, 0, 0)
     torch.cuda.synchronize()
-    ck = ws[: batch * T * 2 * (m + 1) * N * 4].view(torch.float32).view(batch, T, 2, m + 1, N)
+    ck = checkpoints(ws, batch, T, 1, m, N)
     assert torch.equal(ck[:, :, 0], tL) and torch.equal(ck[:, :, 1], tR)
+    assert torch.equal(out, tR[:, T - 1, m] + tL[:, T - 1, m])
 
 
 def branch_signature(fz, llr, w, fp32):
@@ -92,7 +118,8 @@ def branch_signature(fz, llr, w, fp32):
 
 
 @pytest.mark.parametrize("N,T", [(16, 10), (128, 10), (256, 10)])
-def test_gradient_matches_oracle_element_by_element(B, N, T):
+@pytest.mark.parametrize("k", [1, 4, 10])
+def test_gradient_matches_oracle_element_by_element(B, N, T, k):
     """The adjoint of Eq. (1) with per-PE weights, entry by entry.
     * Against the oracle's binary32 adjoint (every operation rounded to binary32, the same
       chain-rule order): the LLR gradient of every codeword and the weight gradient, summed
@@ -100,7 +127,9 @@ def test_gradient_matches_oracle_element_by_element(B, N, T):
     * Against the FP64 adjoint: on codewords whose binary32 forward takes every min and sign
       branch the FP64 forward takes, every entry is within 1e-4 relative or 1e-5 absolute.
       The others are flagged and counted; their dout is zeroed in a second backward pass so
-      that the batch-summed weight gradient is compared over the unflagged codewords alone."""
+      that the batch-summed weight gradient is compared over the unflagged codewords alone.
+    With a checkpoint every k iterations the adjoint recomputes the iterations in between; the
+    results are the same bit for bit for every k."""
     batch = 12
     fz, u, llr, w = inputs(N, T, batch, 40 + N)
     code = B.polarbp_construct(N, N // 2)
@@ -109,11 +138,11 @@ def test_gradient_matches_oracle_element_by_element(B, N, T):
     dout[:, fz == 1] = 0.0
     d_llr = torch.from_numpy(llr).cuda()
     d_w = torch.from_numpy(w).cuda()
-    ws = torch.empty(B.polarbp_wms_workspace(code, batch, T), dtype=torch.uint8, device="cuda")
-    B.polarbp_wms_forward(code, d_llr, d_w, ws)
+    ws = torch.empty(B.polarbp_wms_workspace(code, batch, T, k), dtype=torch.uint8, device="cuda")
+    B.polarbp_wms_forward(code, d_llr, d_w, ws, checkpoint_every=k)
 
     def gpu_backward(d):
-        gw, gl = B.polarbp_wms_backward(code, d_llr, d_w, torch.from_numpy(d).cuda(), ws)
+        gw, gl = B.polarbp_wms_backward(code, d_llr, d_w, torch.from_numpy(d).cuda(), ws, checkpoint_every=k)
         torch.cuda.synchronize()
         return gw.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64)
 
@@ -157,7 +186,7 @@ def test_autograd_function_and_training_step(B):
     w = torch.full((T, m, N // 2), 0.9375, dtype=torch.float32, device="cuda", requires_grad=True)
 
     def loss_fn():
-        out = B.weighted_min_sum(code, d_llr, w)
+        out = B.weighted_min_sum(code, d_llr, w, checkpoint_every=3)
         return torch.nn.functional.binary_cross_entropy_with_logits(-out[:, info], target)
 
     loss = loss_fn()
@@ -181,3 +210,16 @@ def test_autograd_function_and_training_step(B):
         l.backward()
         opt.step()
     assert float(loss_fn().detach()) < first
+
+
+def test_checkpoint_interval_arguments(B):
+    code = B.polarbp_construct(128, 64)
+    d = torch.zeros((4, 128), dtype=torch.float32, device="cuda")
+    w = torch.ones((10, 7, 64), dtype=torch.float32, device="cuda")
+    ws = torch.empty(B.polarbp_wms_workspace(code, 4, 10, 1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.PolarBPError) as e:
+        B.polarbp_wms_forward(code, d, w, ws, checkpoint_every=0)
+    assert e.value.code == B.POLARBP_ERR_ARG
+    # an interval above the iteration count acts as the iteration count: no checkpoint at all
+    assert B.polarbp_wms_workspace(code, 4, 10, 50) == B.polarbp_wms_workspace(code, 4, 10, 10)
+    assert B.polarbp_wms_workspace(code, 4, 10, 10) < B.polarbp_wms_workspace(code, 4, 10, 1)
