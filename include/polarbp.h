@@ -58,9 +58,10 @@ typedef enum polarbp_freeze_mode {
 typedef enum polarbp_thread_mapping {
     POLARBP_MAP_PIPELINED = 0,  /* N/8 sweep threads plus one checker warp that runs the CSFG
                                    checks of iteration t while the sweep runs iteration t+1
-                                   (one codeword per block); the default */
+                                   (one codeword per block); the default for N >= 1024 */
     POLARBP_MAP_BLOCK = 1       /* N/8 threads that sweep, then one of their warps checks while
-                                   the others wait (1, 2 or 4 codewords per block) */
+                                   the others wait (1, 2 or 4 codewords per block); the default
+                                   below N = 1024 */
 } polarbp_thread_mapping;
 
 /* Opaque code handle: the frozen set plus its device-side tables.  Owned by the

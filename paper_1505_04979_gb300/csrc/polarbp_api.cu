@@ -25,7 +25,7 @@ struct polarbp_code {
     uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
     unsigned int* d_status = nullptr;
     int cpc = 1;  // codewords per block of the persistent launch
-    int mapping = POLARBP_MAP_PIPELINED;  // thread mapping when freezing at N = 256 .. 2048
+    int mapping = POLARBP_MAP_PIPELINED;  // thread mapping when freezing at N = 256 .. 2048 (set by construct)
     int bitrev = 0;  // 1: channel position i carries code position rev(i) (Arikan's B_N)
     // polarbp_decode_host's pipeline, created with the handle so that the call
     // itself creates nothing; `pipe_lock` serialises enqueueing on them
@@ -507,6 +507,9 @@ int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polar
     c->N = N;
     c->K = K;
     c->m = m;
+    // default thread mapping: pipelined where it measured faster (N >= 1024; at N = 256 its
+    // checker warp is as large as the one-warp sweep and the block mapping is 1.3x faster)
+    c->mapping = m >= 10 ? POLARBP_MAP_PIPELINED : POLARBP_MAP_BLOCK;
     if (frozen_mask) {
         c->frozen.assign(frozen_mask, frozen_mask + N);
         int nf = 0;

@@ -103,12 +103,14 @@ def test_decode_matches_binary32_oracle(B, N, mode):
 
 @pytest.mark.parametrize("N", [256, 512, 1024, 2048])
 @pytest.mark.parametrize("mode", [(1, 1), (0, 1)])
-def test_block_mapping_matches_binary32_oracle(B, N, mode):
-    """Freezing at N = 256 .. 2048 under the block thread mapping (the sweep warps take turns
-    with the checks) instead of the default pipelined one: the same bits and counts."""
+@pytest.mark.parametrize("mapping", [0, 1])
+def test_both_thread_mappings_match_binary32_oracle(B, N, mode, mapping):
+    """Freezing at N = 256 .. 2048 under each thread mapping (pipelined: a checker warp beside
+    the sweep; block: the sweep warps take turns with the checks), whatever the length's
+    default: the same bits and counts."""
     K = N // 2
     code = B.polarbp_construct(N, K)
-    B.polarbp_set_thread_mapping(code, B.POLARBP_MAP_BLOCK)
+    B.polarbp_set_thread_mapping(code, mapping)
     fz, u, x, llr = host_inputs(N, K, 64, 2.5, 3000 + N)
     uh, it, pe = gpu_decode(B, code, llr, 40, *mode)
     ouh, oit, ope, _ = O.decode_batch(fz, llr, 40, ALPHA, mode[0], mode[1], fp32=True)

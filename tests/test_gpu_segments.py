@@ -117,8 +117,12 @@ def test_autotune_picks_an_admissible_pair(B, N, freeze):
 
 
 def test_thread_mapping_rejects_unknown_values(B):
+    # the defaults: the block mapping below N = 1024, pipelined from there
+    assert B.polarbp_get_thread_mapping(B.polarbp_construct(256, 128)) == B.POLARBP_MAP_BLOCK
+    assert B.polarbp_get_thread_mapping(B.polarbp_construct(512, 256)) == B.POLARBP_MAP_BLOCK
+    assert B.polarbp_get_thread_mapping(B.polarbp_construct(2048, 1024)) == B.POLARBP_MAP_PIPELINED
     code = B.polarbp_construct(1024, 512)
-    assert B.polarbp_get_thread_mapping(code) == B.POLARBP_MAP_PIPELINED  # the default
+    assert B.polarbp_get_thread_mapping(code) == B.POLARBP_MAP_PIPELINED
     with pytest.raises(B.PolarBPError) as e:
         B.polarbp_set_thread_mapping(code, 2)
     assert e.value.code == B.POLARBP_ERR_ARG
