@@ -1192,7 +1192,7 @@ __device__ __forceinline__ void apply_column(Regs<M>& rg, Smem<M>& sm, int tid)
                 if constexpr (LO >= 5) {
 #pragma unroll
                     for (int e = 0; e < G::EL; ++e)
-                        if (e >= e1 && e < e2) bits |= ((xf[(i0 >> 5) + (e << (LO - 5))] >> (i0 & 31)) & 1u) << e;
+                        bits |= ((xf[(i0 >> 5) + (e << (LO - 5))] >> (i0 & 31)) & 1u) << e;
                 } else if constexpr (LO <= 2) {
                     const uint32_t w = xf[i0 >> 5] >> (i0 & 31);
 #pragma unroll
@@ -1206,14 +1206,19 @@ __device__ __forceinline__ void apply_column(Regs<M>& rg, Smem<M>& sm, int tid)
                             if (((e << LO) >> 5) == q) bits |= ((w >> ((e << LO) & 31)) & 1u) << e;
                     }
                 }
+                // elements [e1, e2) take (-1)^bit inf
+                const uint32_t m8 = (0xffu >> (8 - e2)) & ~((1u << e1) - 1u);
                 const int pb = padded_base<M, PH, SH>(tid);
 #pragma unroll
                 for (int e = 0; e < G::EL; ++e) {
-                    if (e >= e1 && e < e2) {
-                        const float v = ((bits >> e) & 1u) ? -INFINITY : INFINITY;
-                        if constexpr (C == M) sm.Lm[i0 + (e << LO)] = v;
-                        else if constexpr (G::is_boundary(C)) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
-                        else rg.Lr[G::rslot(C)][e] = v;
+                    const float v = __uint_as_float(0x7f800000u | ((bits << (31 - e)) & 0x80000000u));
+                    const bool in = (m8 >> e) & 1u;
+                    if constexpr (C == M) {
+                        if (in) sm.Lm[i0 + (e << LO)] = v;
+                    } else if constexpr (G::is_boundary(C)) {
+                        if (in) sm.Lb[G::bslot(C) * G::BUF + pb + padded_off<M, PH, SH>(e)] = v;
+                    } else {
+                        rg.Lr[G::rslot(C)][e] = in ? v : rg.Lr[G::rslot(C)][e];
                     }
                 }
             }

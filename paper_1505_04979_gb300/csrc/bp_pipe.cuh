@@ -226,6 +226,7 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
     int Ps = P;  // lane s (1 <= s < M): P after the check of stage s
     bool first = true;
     int jmin = 1;
+    int jf = 0, p1 = 0;  // stage and end of the iteration's first freeze
 #pragma unroll 1
     while (jmin <= JB && P < N) {
         Spec<M> sp;
@@ -240,7 +241,10 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
             if (sp.lvl[r] == J) sm.Xf[J * NW + (cand >> 5) + sp.w[r]] = sp.x[r];
         freeze_big_fp<M>(sm, J, cand, lane);
         P = cand + (N >> J);
-        if (first) complete_fp<M>(sm, P, J, lane);
+        if (first) {
+            jf = J;
+            p1 = P;
+        }
         if (lane >= J) Ps = P;
         first = false;
         jmin = J + 1;
@@ -273,7 +277,7 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
 #pragma unroll
         for (int i = 0; i < 12; ++i) pa[i] = __shfl_sync(kFull, pw, i);
         unsigned frz = 0u;  // bit jj: stage JS + jj froze
-        int jf = 0, p1 = 0; // stage and end of the first freeze
+        int js = 0;         // stage of the first small freeze
         uint32_t mk = 0u;   // this lane's stage: the frozen CSFG's bits in word wl
 #pragma unroll
         for (int jj = 0; jj < 6; ++jj) {
@@ -284,8 +288,11 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
                 const uint32_t word = off < 32 ? pa[2 * jj] : pa[2 * jj + 1];
                 if ((word >> (off & 31)) & 1u) {
                     if (!frz) {
-                        jf = JS + jj;
-                        p1 = bs + S;
+                        js = JS + jj;
+                        if (first) {
+                            jf = js;
+                            p1 = bs + S;
+                        }
                     }
                     frz |= 1u << jj;
                     if ((lane >> 1) == jj && (bs >> 5) == wl) mk = low_mask(S) << (bs & 31);
@@ -300,7 +307,7 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
             // below it (phase p reads columns 3p+1 .. 3p+3), all but the last one
             int cmin = M + 1;
             if (frz) {
-                cmin = jf;
+                cmin = js;
                 while (cmin > 1 && !(p1 & ((N >> (cmin - 1)) - 1))) --cmin;
             }
             const int pr = cmin >= 4 ? (cmin - 4) / 3 + 1 : 0;
@@ -345,24 +352,23 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
             const unsigned evm = __reduce_or_sync(kFull, ev ? (1u << jl) : 0u);
             if (lane == 0) sm.ctl[CTL_EVENT] |= (int)evm;
             // shared-memory columns (the boundary columns and column M): one position per lane
-            const bool hi_word = P > 32 * (w0 + 1);  // a frozen CSFG reaches word w0 + 1
-#pragma unroll
-            for (int c = JS; c <= M; ++c) {
-                if (smem_column(M, c) && c >= jf) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        if (k == 1 && !hi_word) break;
-                        const int src = 2 * (c - JS) + k;
-                        const uint32_t m = __shfl_sync(kFull, mc, src);
-                        const uint32_t xv = __shfl_sync(kFull, xc, src);
-                        if ((m >> lane) & 1u) put_smem_L<M>(sm, c, 32 * (w0 + k) + lane, (xv >> lane) & 1u);
-                    }
+            const int nk = P > 32 * (w0 + 1) ? 2 : 1;  // a frozen CSFG reaches word w0 + 1
+#pragma unroll 1
+            for (int c = js; c <= M; ++c) {
+                if (!smem_column(M, c)) continue;
+                for (int k = 0; k < nk; ++k) {
+                    const int src = 2 * (c - JS) + k;
+                    const uint32_t m = __shfl_sync(kFull, mc, src);
+                    const uint32_t xv = __shfl_sync(kFull, xc, src);
+                    if ((m >> lane) & 1u) put_smem_L<M>(sm, c, 32 * (w0 + k) + lane, (xv >> lane) & 1u);
                 }
             }
             __syncwarp();
-            if (first) complete_fp<M>(sm, p1, jf, lane);
         }
     }
+    // the enclosing CSFGs the iteration's first freeze completes (later freezes of the same
+    // iteration add less than its size, so they complete none)
+    if (jf > 1 && !(p1 & ((N >> (jf - 1)) - 1))) complete_fp<M>(sm, p1, jf, lane);
     // every feedback value is in place: all phases but the last (which waits for the stop decision)
     release_upto<M>(released, Geo<M>::NP - 1);
     const int pe = (lane >= 1 && lane < M) ? (N - ((Ps >> (M - lane)) << (M - lane))) >> 1 : 0;
