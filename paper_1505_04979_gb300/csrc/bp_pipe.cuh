@@ -301,11 +301,11 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
                 }
             }
         }
+        int cmin = M + 1;
         if (first) {
             // every column this walk still writes is >= cmin: the stage of the first freeze,
             // or of the last CSFG it completes; release the phases that read only columns
             // below it (phase p reads columns 3p+1 .. 3p+3), all but the last one
-            int cmin = M + 1;
             if (frz) {
                 cmin = js;
                 while (cmin > 1 && !(p1 & ((N >> (cmin - 1)) - 1))) --cmin;
@@ -324,8 +324,16 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
             if (act) un = (sm.U[wl] & ~mw) | ((lane & 1) ? v_o : v_e);
             __syncwarp();
             if (lane < 2 && mw) sm.U[wl] = un;
-            // column jl: the CSFGs of stages <= jl frozen now (prefix-or over the stages)
-            uint32_t mc = mk, t;
+            // the enclosing CSFGs of <= 32 positions the first freeze completes (stages cmin ..
+            // js-1, each ending at p1, in word (p1-1)/32): their root columns take the encoding
+            // of their stored bits like the frozen CSFGs' columns do
+            uint32_t mkp = 0u;
+            if (first && act && jl < js && jl >= cmin && ((p1 - 1) >> 5) == wl) {
+                const int Sp = N >> jl;
+                mkp = low_mask(Sp) << ((p1 - Sp) & 31);
+            }
+            // column jl: the CSFGs of stages <= jl frozen or completed now (prefix-or over the stages)
+            uint32_t mc = mk | mkp, t;
             t = __shfl_up_sync(kFull, mc, 2);  if (lane >= 2) mc |= t;
             t = __shfl_up_sync(kFull, mc, 4);  if (lane >= 4) mc |= t;
             t = __shfl_up_sync(kFull, mc, 8);  if (lane >= 8) mc |= t;
@@ -353,8 +361,9 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
             if (lane == 0) sm.ctl[CTL_EVENT] |= (int)evm;
             // shared-memory columns (the boundary columns and column M): one position per lane
             const int nk = P > 32 * (w0 + 1) ? 2 : 1;  // a frozen CSFG reaches word w0 + 1
+            const int c0 = (first && cmin < js) ? (cmin > JS ? cmin : JS) : js;
 #pragma unroll 1
-            for (int c = js; c <= M; ++c) {
+            for (int c = c0; c <= M; ++c) {
                 if (!smem_column(M, c)) continue;
                 for (int k = 0; k < nk; ++k) {
                     const int src = 2 * (c - JS) + k;
@@ -367,8 +376,12 @@ __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, in
         }
     }
     // the enclosing CSFGs the iteration's first freeze completes (later freezes of the same
-    // iteration add less than its size, so they complete none)
-    if (jf > 1 && !(p1 & ((N >> (jf - 1)) - 1))) complete_fp<M>(sm, p1, jf, lane);
+    // iteration add less than its size, so they complete none): after a freeze of <= 32
+    // positions the commit above took those of stages >= M-5, the rest go here
+    {
+        const int jc = (first && jf > JS) ? JS : jf;
+        if (jc > 1 && !(p1 & ((N >> (jc - 1)) - 1))) complete_fp<M>(sm, p1, jc, lane);
+    }
     // every feedback value is in place: all phases but the last (which waits for the stop decision)
     release_upto<M>(released, Geo<M>::NP - 1);
     const int pe = (lane >= 1 && lane < M) ? (N - ((Ps >> (M - lane)) << (M - lane))) >> 1 : 0;
