@@ -439,9 +439,9 @@ int polarbp_awgn_ebn0(const polarbp_code* code, uint64_t seed, uint64_t first_co
  *             recomputes the iterations in between in shared memory with the
  *             forward's arithmetic.  The results do not depend on k; k trades
  *             workspace for recomputation.  k above `iterations` acts as
- *             `iterations`.  With k > 1 the backward holds 3 + 2k message planes
- *             of (m+1) N floats per block: k up to 26 at N = 128, 11 at N = 256,
- *             4 at N = 512, 1 at N = 1024 (POLARBP_ERR_UNSUPPORTED beyond).  The
+ *             `iterations`.  With k > 1 the backward holds 4 + k message planes
+ *             of (m+1) N floats per block: k up to 52 at N = 128, 21 at N = 256,
+ *             7 at N = 512, 1 at N = 1024 (POLARBP_ERR_UNSUPPORTED beyond).  The
  *             forward and the backward of one batch take the same k.
  *   workspace device buffer of polarbp_wms_workspace(code, batch, iterations,
  *             checkpoint_every) bytes: the forward writes its checkpoints there

@@ -21,8 +21,9 @@
 // next, L columns 1..m-1 (R is rebuilt from the channel LLRs every iteration,
 // L[m] is the prior, L[0] is read by nothing), after iterations k-1, 2k-1, ...;
 // the adjoint runs the segments [jk, jk+k) last to first, reloads the
-// checkpoint before the segment and recomputes the segment's L and R planes in
-// shared memory with the forward's own arithmetic.  Every recomputed message
+// checkpoint before the segment, recomputes the segment's L states in shared
+// memory with the forward's own arithmetic and rebuilds each iteration's R plane
+// from its L state when that iteration's adjoint runs.  Every recomputed message
 // equals the forward's bit for bit, so the gradients do not depend on k; k
 // trades workspace (and HBM traffic) for recomputation.  The adjoint writes one
 // gradient partial per codeword, which two more kernels sum over the batch in
@@ -287,9 +288,10 @@ __global__ void wms_backward_kernel(const float* __restrict__ llr, const uint32_
     }
 }
 
-// k > 1: segments [t0, t0 + k) last to first, their planes recomputed from the checkpoint
-// before them.  Shared memory: dL, dLp, dR, then k L planes (Ls + i: the state before
-// iteration t0 + i) and k R planes (Rs + i: R of iteration t0 + i), (m+1) N floats each.
+// k > 1: segments [t0, t0 + k) last to first, their L states recomputed from the checkpoint
+// before them, each iteration's R plane rebuilt when its adjoint runs.  Shared memory: dL,
+// dLp, dR, the R plane, then k L planes (Ls + i: the state before iteration t0 + i),
+// (m+1) N floats each.
 __global__ void wms_backward_seg_kernel(const float* __restrict__ llr, const uint32_t* __restrict__ frozen_words,
                                         const float* __restrict__ w, int N, int m, int T, int k,
                                         const float* __restrict__ ckpt, const float* __restrict__ dout,
@@ -300,8 +302,8 @@ __global__ void wms_backward_seg_kernel(const float* __restrict__ llr, const uin
     float* dL = sh;
     float* dLp = sh + plane;
     float* dR = sh + 2 * plane;
-    float* Ls = sh + 3 * plane;
-    float* Rs = Ls + (size_t)k * plane;
+    float* Rc = sh + 3 * plane;
+    float* Ls = sh + 4 * plane;
     const long long cw = blockIdx.x;
     const float* llr_cw = llr + cw * N;
     const size_t W = (size_t)T * m * (N / 2);
@@ -320,21 +322,19 @@ __global__ void wms_backward_seg_kernel(const float* __restrict__ llr, const uin
             for (int q = threadIdx.x; q < cols; q += blockDim.x) Ls[N + q] = src[q];
         }
         __syncthreads();
-        // iterations t0 .. t0 + len - 1 with the forward's arithmetic: L states and R planes
-        for (int i = 0; i < len; ++i) {
-            float* Ri = Rs + (size_t)i * plane;
-            if (i + 1 < len) {
-                float* Ln = Ls + (size_t)(i + 1) * plane;
-                for (int q = threadIdx.x; q < plane; q += blockDim.x) Ln[q] = Ln[q - plane];
-                __syncthreads();
-                wms_iteration(Ln, Ri, llr_cw, w, N, m, t0 + i);
-            } else {
-                wms_rebuild_R(Ls + (size_t)i * plane, Ri, llr_cw, w, N, m, t0 + i);
-            }
+        // the segment's later L states with the forward's arithmetic (Rc is scratch here)
+        for (int i = 1; i < len; ++i) {
+            float* Li = Ls + (size_t)i * plane;
+            for (int q = threadIdx.x; q < plane; q += blockDim.x) Li[q] = Li[q - plane];
+            __syncthreads();
+            wms_iteration(Li, Rc, llr_cw, w, N, m, t0 + i - 1);
         }
-        for (int i = len - 1; i >= 0; --i)
-            wms_backward_iteration(Ls + (size_t)i * plane, Rs + (size_t)i * plane, dL, dLp, dR, frozen_words, w, N, m,
-                                   T, t0 + i, dout + cw * N, partial + cw * W, dl_acc);
+        for (int i = len - 1; i >= 0; --i) {
+            const float* Lp = Ls + (size_t)i * plane;
+            wms_rebuild_R(Lp, Rc, llr_cw, w, N, m, t0 + i);
+            wms_backward_iteration(Lp, Rc, dL, dLp, dR, frozen_words, w, N, m, T, t0 + i, dout + cw * N,
+                                   partial + cw * W, dl_acc);
+        }
     }
     for (int j = 0; j < 4; ++j) {
         const int i = threadIdx.x + j * blockDim.x;
@@ -408,7 +408,7 @@ WmsLayout wms_layout(int N, int m, int batch, int T, int k)
 
 constexpr size_t kMaxBlockSmem = 227 * 1024;
 
-size_t backward_smem(int N, int m, int k) { return (size_t)(k == 1 ? 3 : 3 + 2 * k) * (m + 1) * N * sizeof(float); }
+size_t backward_smem(int N, int m, int k) { return (size_t)(k == 1 ? 3 : 4 + k) * (m + 1) * N * sizeof(float); }
 
 // Checks the arguments; *k becomes the effective checkpoint interval min(k, T).
 int wms_args(const polarbp_code* c, int batch, int T, int* k, int* N, int* m)
