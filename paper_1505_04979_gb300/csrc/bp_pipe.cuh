@@ -214,7 +214,11 @@ __device__ __forceinline__ void release_upto(int& released, int upto)
 // word w0 + k.  Column c of every CSFG of stage j <= c frozen now is the new
 // stored bits encoded through the butterflies of stages M-1 .. c (steps 1 .. S_c/2,
 // which stay inside each aligned CSFG of stage <= c); the columns of one stage
-// cover the union of those CSFGs, a contiguous range.
+// cover the union of those CSFGs, a contiguous range.  The enclosing CSFGs of
+// <= 32 positions that the first freeze completes join that commit (their root
+// column is the same encoding of their stored bits); larger ones go through
+// complete_fp.  The kernel is bound by instruction fetch as much as by issue, so
+// the walk keeps one copy of each rare path.
 template <int M>
 __device__ __forceinline__ int walk_pipe(Smem<M>& sm, const SpecSlots<M>& ss, int& P, int lane, int& released)
 {
