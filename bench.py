@@ -431,6 +431,7 @@ def run_ours(args):
                                     "lane instructions per PE update"),
                      "algorithmic_bytes_per_launch": batch * (4 * N + N + 12)},
         "modes": per_mode,
+        "equal_fer": equal_fer(per_mode) if all(m in per_mode for m in ("fixed", "gstop", "gstop_freeze")) else None,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -439,6 +440,25 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def equal_fer(per_mode):
+    """The metric's comparison made explicit: G-stop + freezing against fixed iterations and
+    against G-stop alone on the same codewords, with the Wilson 95 % intervals of their FER
+    (disjoint intervals mean the FERs differ) and the throughput ratio."""
+    head = per_mode["gstop_freeze"]
+    out = {}
+    for other in ("fixed", "gstop"):
+        o = per_mode[other]
+        lo_h, hi_h = head["fer_ci95"]
+        lo_o, hi_o = o["fer_ci95"]
+        out[f"vs_{other}"] = {
+            "fer": head["fer"], "fer_other": o["fer"],
+            "ci_overlap": not (hi_h < lo_o or hi_o < lo_h),
+            "fer_lower": head["fer"] < o["fer"],
+            "throughput_ratio": head["info_gbit_s"] / o["info_gbit_s"],
+        }
+    return out
 
 
 MIXED_CLASSES = [(256, 64), (256, 128), (256, 192), (1024, 256), (1024, 512), (1024, 768), (4096, 1024),
