@@ -53,7 +53,7 @@ typedef enum polarbp_freeze_mode {
 } polarbp_freeze_mode;
 
 /* How the threads of a block share one codeword's work when freezing
- * (POLARBP_FREEZE_CSFG) at N = 256 .. 2048.  Decisions, iteration and PE counts
+ * (POLARBP_FREEZE_CSFG) at N = 256 .. 4096.  Decisions, iteration and PE counts
  * are the same under both; only the schedule differs. */
 typedef enum polarbp_thread_mapping {
     POLARBP_MAP_PIPELINED = 0,  /* N/8 sweep threads plus one checker warp that runs the CSFG
@@ -396,7 +396,7 @@ int polarbp_get_codewords_per_block(const polarbp_code* code, int* codewords_per
 
 /* polarbp_set_thread_mapping / polarbp_get_thread_mapping -- the thread mapping
  * (polarbp_thread_mapping) that polarbp_decode, polarbp_decode_host and
- * polarbp_decode_segments use for this code when freezing at N = 256 .. 2048.
+ * polarbp_decode_segments use for this code when freezing at N = 256 .. 4096.
  * The pipelined mapping holds one codeword per block: with codewords per block
  * above 1 the persistent launch takes the block mapping.  polarbp_decode_mixed
  * always takes the block mapping.  Errors: POLARBP_ERR_ARG (NULL handle, unknown

@@ -1483,7 +1483,7 @@ struct LaunchReq {
     int stop_mode;
     int freeze_mode;
     bool trace;
-    bool pipelined = true;  // freezing at N = 256 .. 2048: the checker-warp mapping (bp_pipe.cuh)
+    bool pipelined = true;  // freezing at N = 256 .. 4096: the checker-warp mapping (bp_pipe.cuh)
     cudaStream_t stream;
 };
 
@@ -1529,7 +1529,7 @@ struct SegLaunch {
     int stop_mode;
     int freeze_mode;
     int cpc;
-    bool pipelined = true;  // freezing at N = 256 .. 2048 with cpc 1: the checker-warp mapping (bp_pipe.cuh)
+    bool pipelined = true;  // freezing at N = 256 .. 4096 with cpc 1: the checker-warp mapping (bp_pipe.cuh)
     int sms;
     cudaStream_t stream;
 };

@@ -1,5 +1,5 @@
 // bp_pipe.cuh -- pipelined min-sum BP decoding of polar codes with the G-matrix
-// stop and CSFG freezing (reading A), N = 256 .. 2048, one codeword per block.
+// stop and CSFG freezing (reading A), N = 256 .. 4096, one codeword per block.
 //
 // Method: arXiv 1505.04979, Eq. (1) (Sec. II-A), the CSFG check, freezing order
 // and +-inf feedback of Sec. III (Eqs. (2)-(4)), the PE count of Sec. IV.  The
@@ -598,12 +598,12 @@ cudaError_t launch_pipe(const DecodeArgs& args, cudaStream_t stream)
 }
 
 // Decode launches of one code length: G-stop + freezing and freezing alone
-// (reading A, without message planes) run pipelined for N = 256 .. 2048 unless
+// (reading A, without message planes) run pipelined for N = 256 .. 4096 unless
 // the code asks for the one-block mapping, the rest on bp_decode_kernel.
 template <int M>
 cudaError_t launch_decode_pipe(const LaunchReq& q)
 {
-    if constexpr (M >= 8 && M <= 11) {
+    if constexpr (M >= 8 && M <= 12) {
         if (q.freeze_mode == 1 && !q.trace && q.pipelined)
             return q.stop_mode ? launch_pipe<M, true>(q.args, q.stream) : launch_pipe<M, false>(q.args, q.stream);
     }
@@ -643,12 +643,12 @@ cudaError_t launch_pipe_persistent(const SegLaunch& q)
 }
 
 // Persistent launches of one code length: the pipelined mapping for freezing
-// (reading A) at N = 256 .. 2048 with one codeword per block, unless the code
+// (reading A) at N = 256 .. 4096 with one codeword per block, unless the code
 // asks for the one-block mapping; otherwise bp_decode_persistent.
 template <int M>
 cudaError_t launch_persistent_pipe(const SegLaunch& q)
 {
-    if constexpr (M >= 8 && M <= 11) {
+    if constexpr (M >= 8 && M <= 12) {
         if (q.freeze_mode == 1 && q.pipelined && q.cpc == 1)
             return q.stop_mode ? launch_pipe_persistent<M, true>(q) : launch_pipe_persistent<M, false>(q);
     }

@@ -25,7 +25,7 @@ struct polarbp_code {
     uint32_t* d_frozen = nullptr;  // ceil(N/32) words, bit i = frozen[i]
     unsigned int* d_status = nullptr;
     int cpc = 1;  // codewords per block of the persistent launch
-    int mapping = POLARBP_MAP_PIPELINED;  // thread mapping when freezing at N = 256 .. 2048 (set by construct)
+    int mapping = POLARBP_MAP_PIPELINED;  // thread mapping when freezing at N = 256 .. 4096 (set by construct)
     int bitrev = 0;  // 1: channel position i carries code position rev(i) (Arikan's B_N)
     // polarbp_decode_host's pipeline, created with the handle so that the call
     // itself creates nothing; `pipe_lock` serialises enqueueing on them
@@ -916,8 +916,8 @@ int polarbp_autotune(polarbp_code* c, int max_iter, float scale, int stop_mode, 
     float best_ms = 3.4e38f;
     if (rc == POLARBP_OK) rc = polarbp_awgn(c, 1, 0, B, 2.5f, nullptr, d_llr, stream);
     // candidates (mapping, codewords per block); the pipelined mapping exists for freezing
-    // (reading A) at N = 256 .. 2048 with one codeword per block
-    const bool pipe_ok = freeze_mode == POLARBP_FREEZE_CSFG && c->m <= 11;
+    // (reading A) at N = 256 .. 4096 with one codeword per block
+    const bool pipe_ok = freeze_mode == POLARBP_FREEZE_CSFG && c->m <= 12;
     const std::pair<int, int> cands[] = {{POLARBP_MAP_PIPELINED, 1}, {POLARBP_MAP_BLOCK, 1}, {POLARBP_MAP_BLOCK, 2},
                                          {POLARBP_MAP_BLOCK, 4}};
     for (const auto& cand : cands) {

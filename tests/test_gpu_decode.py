@@ -101,17 +101,17 @@ def test_decode_matches_binary32_oracle(B, N, mode):
         assert np.array_equal(uh, ouh)
 
 
-@pytest.mark.parametrize("N", [256, 512, 1024, 2048])
+@pytest.mark.parametrize("N", [256, 512, 1024, 2048, 4096])
 @pytest.mark.parametrize("mode", [(1, 1), (0, 1)])
 @pytest.mark.parametrize("mapping", [0, 1])
 def test_both_thread_mappings_match_binary32_oracle(B, N, mode, mapping):
-    """Freezing at N = 256 .. 2048 under each thread mapping (pipelined: a checker warp beside
+    """Freezing at N = 256 .. 4096 under each thread mapping (pipelined: a checker warp beside
     the sweep; block: the sweep warps take turns with the checks), whatever the length's
     default: the same bits and counts."""
     K = N // 2
     code = B.polarbp_construct(N, K)
     B.polarbp_set_thread_mapping(code, mapping)
-    fz, u, x, llr = host_inputs(N, K, 64, 2.5, 3000 + N)
+    fz, u, x, llr = host_inputs(N, K, 64 if N < 4096 else 16, 2.5, 3000 + N)
     uh, it, pe = gpu_decode(B, code, llr, 40, *mode)
     ouh, oit, ope, _ = O.decode_batch(fz, llr, 40, ALPHA, mode[0], mode[1], fp32=True)
     assert np.array_equal(it, oit) and np.array_equal(pe, ope) and np.array_equal(uh, ouh)
