@@ -3,7 +3,8 @@
 //
 // Method: arXiv 1505.04979, Eq. (1) (Sec. II-A), the CSFG freezing of Sec. III
 // and the G-matrix stop; each codeword is decoded by decode_codeword of
-// bp_decode.cuh and retires at its own stop.
+// bp_decode.cuh (or, for N = 4096 with freezing, decode_pipe_codeword of
+// bp_pipe.cuh) and retires at its own stop.
 //
 // Shape.  The launch is specialised on the longest length 2^MT in the stream.
 // A block has Geo<MT>::BLOCK threads and 8800 x 2^(MT-8) bytes of shared
@@ -17,18 +18,25 @@
 // does.  Barriers: the block barrier for the top length, named barriers
 // 1 + (2^d - 2) + g for the groups g of depth d = MT - M in 1..3 (disjoint, since
 // groups of different depths run at once), warp synchronisation for N = 256.
+// With freezing and N = 4096 on top, the block has one warp more and decodes the
+// N = 4096 codewords pipelined (a checker warp beside the 16 sweep warps, the
+// named barriers of bp_pipe.cuh, every one complete before the block barrier
+// that ends the length); that warp idles through the shorter lengths.
 #pragma once
 
-#include "bp_decode.cuh"
+#include "bp_pipe.cuh"
 
 namespace polarbp {
 
 constexpr int kMixedSlice8 = 8800;  // bytes of shared memory per N = 256 group
 
-template <int MT>
+template <int MT, bool FREEZE>
 struct MixedTop {
-    static constexpr int THREADS = Geo<MT>::BLOCK;
-    static constexpr int SMEM = kMixedSlice8 << (MT - 8);
+    static constexpr bool PIPE = FREEZE && MT == 12;  // the top length runs pipelined
+    static constexpr int THREADS = PIPE ? PipeGeo<MT>::THREADS : Geo<MT>::BLOCK;
+    static constexpr int SLICES = kMixedSlice8 << (MT - 8);
+    static constexpr int PBYTES = PIPE ? (int)PipeLayout<MT>::bytes : 0;
+    static constexpr int SMEM = PBYTES > SLICES ? PBYTES : SLICES;
     // blocks per SM the kernel is compiled for: 640 threads per SM, the one-length kernels' bound
     // (the tighter bound they take for N = 1024 with freezing spills the shorter lengths' decoders)
     static constexpr int MIN_BLOCKS = (640 / THREADS) < 1 ? 1 : (640 / THREADS);
@@ -37,10 +45,10 @@ struct MixedTop {
 template <int MT, int M>
 struct MixedShape {
     static constexpr int BLOCK = Geo<M>::BLOCK;
-    static constexpr int CPC = MixedTop<MT>::THREADS / BLOCK;
+    static constexpr int CPC = Geo<MT>::BLOCK / BLOCK;
     static constexpr int SLICE = kMixedSlice8 << (M - 8);
     static constexpr int BAR0 = CPC - 2;  // group_sync's named barrier is 1 + BAR0 + g
-    static_assert(BLOCK * CPC == MixedTop<MT>::THREADS && SLICE * CPC == MixedTop<MT>::SMEM, "groups tile the block");
+    static_assert(BLOCK * CPC == Geo<MT>::BLOCK && SLICE * CPC == (kMixedSlice8 << (MT - 8)), "groups tile the block");
     static_assert(SLICE % 32 == 0 && (size_t)SLICE >= SmemLayout<M>::bytes, "a group's slice holds its decoder");
     static_assert(CPC == 1 || BLOCK == 32 || BAR0 + CPC <= 15, "named barriers 1..15");
 };
@@ -57,6 +65,7 @@ __device__ __forceinline__ void mixed_drain(const SegArgs& a, unsigned char* sme
     using SH = MixedShape<MT, M>;
     constexpr int N = Geo<M>::N, BLOCK = SH::BLOCK, CPC = SH::CPC;
     if (a.total == 0) return;
+    if (threadIdx.x >= Geo<MT>::BLOCK) return;  // the pipelined top length's checker warp
     const int grp = threadIdx.x / BLOCK;
     const int tid = threadIdx.x % BLOCK;
     const int bar = SH::BAR0 + grp;
@@ -85,15 +94,48 @@ __device__ __forceinline__ void mixed_drain(const SegArgs& a, unsigned char* sme
     group_sync<BLOCK, CPC>(bar);  // every thread of the group has read its last pop
 }
 
+// The top length pipelined (bp_pipe.cuh): the whole block takes one codeword at a time.
+template <int MT, bool GSTOP>
+__device__ __forceinline__ void mixed_drain_pipe(const SegArgs& a, unsigned char* smem_raw)
+{
+    constexpr int N = Geo<MT>::N;
+    if (a.total == 0) return;
+    Smem<MT> sm(smem_raw);
+    int* qslot = sm.ctl + CTL_Q;
+    for (;;) {
+        __syncthreads();  // the previous codeword's readers are done with shared memory
+        if (threadIdx.x == 0) *qslot = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = *qslot;
+        if (q >= a.total) break;
+        int sg = 0;
+        while (sg + 1 < a.nseg && q >= a.start[sg + 1]) ++sg;
+        const long long r = q - a.start[sg];
+        const CwIO io{a.llr[sg] + r * N,
+                      a.frozen_words[sg],
+                      a.u_hat[sg] + r * N,
+                      a.iters[sg] ? a.iters[sg] + r : nullptr,
+                      a.pe[sg] ? a.pe[sg] + r : nullptr,
+                      nullptr,
+                      nullptr,
+                      nullptr,
+                      a.bitrev[sg]};
+        __syncthreads();  // every thread has read the popped index before the decode reuses the slot
+        decode_pipe_codeword<MT, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
+    }
+    __syncthreads();  // the shorter lengths reuse the shared memory
+}
+
 template <int MT, int M, bool GSTOP, bool FREEZE>
 __device__ __forceinline__ void mixed_drain_down(const MixedArgs& a, unsigned char* smem_raw)
 {
-    mixed_drain<MT, M, GSTOP, FREEZE>(a.seg[M - 8], smem_raw);
+    if constexpr (M == MT && MixedTop<MT, FREEZE>::PIPE) mixed_drain_pipe<MT, GSTOP>(a.seg[M - 8], smem_raw);
+    else mixed_drain<MT, M, GSTOP, FREEZE>(a.seg[M - 8], smem_raw);
     if constexpr (M > 8) mixed_drain_down<MT, M - 1, GSTOP, FREEZE>(a, smem_raw);
 }
 
 template <int MT, bool GSTOP, bool FREEZE>
-__global__ void __launch_bounds__(MixedTop<MT>::THREADS, MixedTop<MT>::MIN_BLOCKS)
+__global__ void __launch_bounds__(MixedTop<MT, FREEZE>::THREADS, MixedTop<MT, FREEZE>::MIN_BLOCKS)
     bp_decode_mixed(MixedArgs a)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -104,7 +146,7 @@ template <int MT, bool GSTOP, bool FREEZE>
 cudaError_t launch_mixed_one(const MixedArgs& args, int sms, cudaStream_t stream)
 {
     auto kern = bp_decode_mixed<MT, GSTOP, FREEZE>;
-    constexpr int threads = MixedTop<MT>::THREADS, smem = MixedTop<MT>::SMEM;
+    constexpr int threads = MixedTop<MT, FREEZE>::THREADS, smem = MixedTop<MT, FREEZE>::SMEM;
     // blocks per SM, per device, set with the shared-memory attribute on the device's first launch
     constexpr int kDevices = 64;
     static std::atomic<int> blocks_per_sm[kDevices];
