@@ -121,7 +121,7 @@ __device__ __forceinline__ void mixed_drain_pipe(const SegArgs& a, unsigned char
                       nullptr,
                       a.bitrev[sg]};
         __syncthreads();  // every thread has read the popped index before the decode reuses the slot
-        decode_pipe_codeword<MT, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
+        decode_pipe_codeword_call<MT, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
     }
     __syncthreads();  // the shorter lengths reuse the shared memory
 }
