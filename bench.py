@@ -73,7 +73,8 @@ PEAK_PE_PER_S = SMS * LANES * SM_MAX_HZ / OPS_PER_PE
 MODES = {"fixed": (0, 0), "gstop": (1, 0), "freeze": (0, 1), "gstop_freeze": (1, 1)}
 PROFILE = os.path.join(ROOT, "profiles", "bp_decode_pipe_n1024_ebn0_3db.md")
 # the headline kernel's sources: the pipelined decoder and the sweep it shares
-KERNEL_SRCS = [os.path.join(ROOT, "paper_1505_04979_gb300", "csrc", f) for f in ("bp_pipe.cuh", "bp_decode.cuh")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1505_04979_gb300", "csrc", f)
+               for f in ("bp_pipe.cuh", "bp_decode.cuh", "checked.cuh")]
 
 
 def kernel_source_sha256() -> str:

@@ -38,7 +38,9 @@ typedef enum polarbp_status {
                                     spins on a flag (work queues use atomics, the cluster decoder
                                     hardware cluster barriers), so no call returns it */
     POLARBP_ERR_NOMEM = 5,       /* a library allocation failed */
-    POLARBP_ERR_UNSUPPORTED = 6  /* valid arguments the library has no kernel for */
+    POLARBP_ERR_UNSUPPORTED = 6, /* valid arguments the library has no kernel for */
+    POLARBP_ERR_CHECK = 7        /* checked build only: a decode stored into a shared-memory
+                                    redzone, i.e. outside the region it meant (polarbp_get_status) */
 } polarbp_status;
 
 typedef enum polarbp_stop_mode {
@@ -466,16 +468,24 @@ int polarbp_wms_backward(const polarbp_code* code, const float* llr, int batch, 
                          size_t workspace_bytes, void* stream);
 
 /*
- * polarbp_get_status -- read and clear the handle's device status word.  Waits
+ * polarbp_get_status -- read and clear the handle's device status words.  Waits
  * for `stream`.  Returns POLARBP_ERR_NONFINITE when a decode since the last
  * call saw a non-finite LLR, else POLARBP_OK (or POLARBP_ERR_CUDA).
+ * In the checked build (compiled with POLARBP_CHECKED; polarbp_version then
+ * ends in "checked"), the shared memory of every decode of polarbp_decode,
+ * _trace, _host, _segments and _mixed has a 256-byte redzone before its first
+ * region and after each region, filled before the decode's first store and
+ * compared after its last; a changed redzone word makes this call return
+ * POLARBP_ERR_CHECK (before POLARBP_ERR_NONFINITE), with a message that gives
+ * the number of changed words and the layout, redzone and byte offset of the
+ * first.  The default build has no redzones and never returns it.
  */
 int polarbp_get_status(const polarbp_code* code, void* stream);
 
 /* polarbp_last_error -- message of the calling thread's last failure ("" if none). */
 const char* polarbp_last_error(void);
 
-/* polarbp_version -- library version string. */
+/* polarbp_version -- library version string ("... checked" for the checked build). */
 const char* polarbp_version(void);
 
 #ifdef __cplusplus

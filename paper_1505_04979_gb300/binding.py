@@ -3,7 +3,8 @@
 Argument marshalling only: tensors are passed as ``data_ptr()`` together with
 torch's current CUDA stream; every step of decoding runs in the CUDA library.
 There is no CPU fallback: if ``libpolarbp.so`` is missing or fails to load, the
-calls raise.
+calls raise.  The environment variable POLARBP_LIBRARY, when set, names another
+build of the library to load instead (the checked build, libpolarbp_checked.so).
 """
 from __future__ import annotations
 
@@ -14,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpolarbp.so")
+LIB_PATH = os.environ.get("POLARBP_LIBRARY") or os.path.join(_HERE, "libpolarbp.so")
 
 POLARBP_OK = 0
 POLARBP_ERR_ARG = 1
@@ -23,6 +24,7 @@ POLARBP_ERR_CUDA = 3
 POLARBP_ERR_TIMEOUT = 4
 POLARBP_ERR_NOMEM = 5
 POLARBP_ERR_UNSUPPORTED = 6
+POLARBP_ERR_CHECK = 7
 POLARBP_STOP_NONE = 0
 POLARBP_STOP_GMATRIX = 1
 POLARBP_FREEZE_OFF = 0
@@ -431,7 +433,8 @@ def polarbp_decode_host_noalloc(code: PolarCode, llr_host, max_iter: int, scale:
 
 
 def polarbp_get_status(code: PolarCode, stream=None) -> int:
-    """POLARBP_OK, or POLARBP_ERR_NONFINITE when a decode saw a non-finite LLR (clears the flag)."""
+    """POLARBP_OK, or POLARBP_ERR_NONFINITE when a decode saw a non-finite LLR (clears the flag).
+    A redzone store seen by the checked build raises PolarBPError with code POLARBP_ERR_CHECK."""
     rc = lib().polarbp_get_status(code.handle, _stream(stream))
     if rc not in (POLARBP_OK, POLARBP_ERR_NONFINITE):
         _check(rc, "polarbp_get_status")

@@ -79,18 +79,47 @@ enum : int {
 template <int XC>
 struct CLayout {
     using G = CGeo<XC>;
+    static constexpr size_t RZ = kRedzone;  // redzone after each region (checked build only)
     static constexpr size_t off_Lx = SmemLayout<12>::bytes;                     // [XC][n] L columns 1..XC
-    static constexpr size_t off_LlrP = off_Lx + sizeof(float) * XC * G::n;      // partner's channel LLRs
-    static constexpr size_t off_Xw = off_LlrP + sizeof(float) * G::n;           // [XC+1][NWL] decisions
-    static constexpr size_t off_V = off_Xw + 4 * (XC + 1) * G::NWL;             // [XC][NWL] Eq. (3) of the part
-    static constexpr size_t off_Uc = off_V + 4 * XC * G::NWL;                   // [XC][NWL] combined Eq. (3)
-    static constexpr size_t off_XfX = off_Uc + 4 * XC * G::NWL;                 // [XC][NWL] feedback decisions
-    static constexpr size_t off_Wg = off_XfX + 4 * XC * G::NWL;                 // [NWL] u_hat transform
-    static constexpr size_t off_UE = off_Wg + 4 * G::NWL;                       // [NWL] stored bits transform
-    static constexpr size_t off_Fb = off_UE + 4 * G::NWL;                       // [FBW] failure bitmaps
-    static constexpr size_t off_Cc = off_Fb + 4 * G::FBW;
-    static constexpr size_t bytes = off_Cc + 4 * CC_INTS;
+    static constexpr size_t end_Lx = off_Lx + sizeof(float) * XC * G::n;
+    static constexpr size_t off_LlrP = end_Lx + RZ;                             // partner's channel LLRs
+    static constexpr size_t end_LlrP = off_LlrP + sizeof(float) * G::n;
+    static constexpr size_t off_Xw = end_LlrP + RZ;                             // [XC+1][NWL] decisions
+    static constexpr size_t end_Xw = off_Xw + 4 * (XC + 1) * G::NWL;
+    static constexpr size_t off_V = end_Xw + RZ;                                // [XC][NWL] Eq. (3) of the part
+    static constexpr size_t end_V = off_V + 4 * XC * G::NWL;
+    static constexpr size_t off_Uc = end_V + RZ;                                // [XC][NWL] combined Eq. (3)
+    static constexpr size_t end_Uc = off_Uc + 4 * XC * G::NWL;
+    static constexpr size_t off_XfX = end_Uc + RZ;                              // [XC][NWL] feedback decisions
+    static constexpr size_t end_XfX = off_XfX + 4 * XC * G::NWL;
+    static constexpr size_t off_Wg = end_XfX + RZ;                              // [NWL] u_hat transform
+    static constexpr size_t end_Wg = off_Wg + 4 * G::NWL;
+    static constexpr size_t off_UE = end_Wg + RZ;                               // [NWL] stored bits transform
+    static constexpr size_t end_UE = off_UE + 4 * G::NWL;
+    static constexpr size_t off_Fb = end_UE + RZ;                               // [FBW] failure bitmaps
+    static constexpr size_t end_Fb = off_Fb + 4 * G::FBW;
+    static constexpr size_t off_Cc = end_Fb + RZ;
+    static constexpr size_t end_Cc = off_Cc + 4 * CC_INTS;
+    static constexpr size_t bytes = end_Cc + RZ;
+    static constexpr int ZONES = 10;
+    __host__ __device__ static constexpr size_t zone(int k)
+    {
+        return k == 0 ? end_Lx : k == 1 ? end_LlrP : k == 2 ? end_Xw : k == 3 ? end_V : k == 4 ? end_Uc
+             : k == 5 ? end_XfX : k == 6 ? end_Wg : k == 7 ? end_UE : k == 8 ? end_Fb : end_Cc;
+    }
 };
+
+// Fill (FILL) or compare every redzone of a CLayout<XC> at base.
+template <int XC, bool FILL>
+__device__ __forceinline__ void cluster_redzones(unsigned char* base, unsigned int* status, int tid, int stride)
+{
+    if constexpr (kChecked) {
+        redzones<12, FILL>(base, status, tid, stride);
+#pragma unroll 1
+        for (int k = 0; k < CLayout<XC>::ZONES; ++k)
+            redzone_pass<FILL>(base, CLayout<XC>::zone(k), kLayoutCluster, k, status, tid, stride);
+    }
+}
 
 template <int XC>
 struct CSmem {
@@ -299,6 +328,7 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
     CSmem<XC> cs(smem_raw);
     sm.L0 = cs.Lcol(XC);
     const int base = r * n;  // first code position of this block's part
+    cluster_redzones<XC, true>(smem_raw, a.status, tid, T);
 
     const float* llr = a.llr + cw * N;
     const long long tb0 = TRACE ? cw * a.max_iter * (long long)(M + 1) * N : 0;
@@ -738,6 +768,8 @@ __global__ void __launch_bounds__(512, 1) bp_decode_cluster(DecodeArgs a)
         if (a.iters) a.iters[cw] = iters;
         if (a.pe) a.pe[cw] = (GSTOP || FREEZE) ? *cs.pe_acc() : (long long)iters * M * (N >> 1);
     }
+    // every shared-memory store of the cluster precedes its last barrier
+    cluster_redzones<XC, false>(smem_raw, a.status, tid, T);
 }
 
 template <int XC, bool GSTOP, bool FREEZE, bool TRACE>

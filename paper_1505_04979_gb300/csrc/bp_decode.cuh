@@ -33,6 +33,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "checked.cuh"
+
 namespace polarbp {
 
 constexpr uint32_t kFull = 0xffffffffu;
@@ -177,26 +179,57 @@ __device__ __forceinline__ void group_sync(int grp)
     }
 }
 
+// Byte offsets of one decode's shared memory.  RZ is the redzone of the checked
+// build (0 otherwise): one before the first region and one after each region.
 template <int M>
 struct SmemLayout {
     using G = Geo<M>;
     static constexpr int N = G::N, NW = G::NW;
-    static constexpr size_t off_Lb = 0;
-    static constexpr size_t off_Rx = off_Lb + sizeof(float) * G::NB * G::BUF;
-    static constexpr size_t off_Llr = (off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * G::BUF + 15) / 16 * 16;
-    static constexpr size_t off_U = off_Llr + sizeof(float) * G::N;
-    static constexpr size_t off_Fz = off_U + sizeof(uint32_t) * NW;
-    static constexpr size_t off_Xf = off_Fz + sizeof(uint32_t) * NW;
-    static constexpr size_t off_Ctl = (off_Xf + sizeof(uint32_t) * (M + 1) * NW + 15) / 16 * 16;
+    static constexpr size_t RZ = kRedzone;
+    static constexpr size_t off_Lb = RZ;
+    static constexpr size_t end_Lb = off_Lb + sizeof(float) * G::NB * G::BUF;
+    static constexpr size_t off_Rx = end_Lb + RZ;
+    static constexpr size_t end_Rx = off_Rx + sizeof(float) * (G::NP > 1 ? 2 : 0) * G::BUF;
+    static constexpr size_t off_Llr = (end_Rx + RZ + 15) / 16 * 16;
+    static constexpr size_t end_Llr = off_Llr + sizeof(float) * G::N;
+    static constexpr size_t off_U = end_Llr + RZ;
+    static constexpr size_t end_U = off_U + sizeof(uint32_t) * NW;
+    static constexpr size_t off_Fz = end_U + RZ;
+    static constexpr size_t end_Fz = off_Fz + sizeof(uint32_t) * NW;
+    static constexpr size_t off_Xf = end_Fz + RZ;
+    static constexpr size_t end_Xf = off_Xf + sizeof(uint32_t) * (M + 1) * NW;
+    static constexpr size_t off_Ctl = (end_Xf + RZ + 15) / 16 * 16;
     static constexpr int CTL_INTS = CTL_EV + 2 * (M + 1);
-    static constexpr size_t off_Hd = (off_Ctl + sizeof(int) * CTL_INTS + 15) / 16 * 16;
+    static constexpr size_t end_Ctl = off_Ctl + sizeof(int) * CTL_INTS;
+    static constexpr size_t off_Hd = (end_Ctl + RZ + 15) / 16 * 16;
     static constexpr size_t hd_bytes = (size_t)(M + 1) * G::HDS;
+    static constexpr size_t end_Hd = off_Hd + hd_bytes;
     // two NW-word buffers for the encoding of the channel-side decisions
-    static constexpr size_t off_Ge = (off_Hd + hd_bytes + 15) / 16 * 16;
+    static constexpr size_t off_Ge = (end_Hd + RZ + 15) / 16 * 16;
+    static constexpr size_t end_Ge = off_Ge + 2 * sizeof(uint32_t) * NW;
     // column M in natural order; 32-byte aligned so each thread's 8 entries load as two float4
-    static constexpr size_t off_Lm = (off_Ge + 2 * sizeof(uint32_t) * NW + 31) / 32 * 32;
-    static constexpr size_t bytes = (off_Lm + sizeof(float) * N + 15) / 16 * 16;
+    static constexpr size_t off_Lm = (end_Ge + RZ + 31) / 32 * 32;
+    static constexpr size_t end_Lm = off_Lm + sizeof(float) * N;
+    static constexpr size_t bytes = (end_Lm + RZ + 15) / 16 * 16;
+    // redzone k starts at zone(k) (k = 0: before Lb; k >= 1: after the k-th region)
+    static constexpr int ZONES = 11;
+    __host__ __device__ static constexpr size_t zone(int k)
+    {
+        return k == 0 ? 0 : k == 1 ? end_Lb : k == 2 ? end_Rx : k == 3 ? end_Llr : k == 4 ? end_U : k == 5 ? end_Fz
+             : k == 6 ? end_Xf : k == 7 ? end_Ctl : k == 8 ? end_Hd : k == 9 ? end_Ge : end_Lm;
+    }
 };
+
+// Fill (FILL) or compare the redzones of a SmemLayout<M> at base.
+template <int M, bool FILL>
+__device__ __forceinline__ void redzones(unsigned char* base, unsigned int* status, int tid, int stride)
+{
+    if constexpr (kChecked) {
+#pragma unroll 1
+        for (int k = 0; k < SmemLayout<M>::ZONES; ++k)
+            redzone_pass<FILL>(base, SmemLayout<M>::zone(k), kLayoutBlock, k, status, tid, stride);
+    }
+}
 
 template <int M>
 struct Smem {
@@ -1308,6 +1341,7 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
     const int lane = tid & 31;
     const bool worker = tid < T;
 
+    redzones<M, true>(smem_raw, status, tid, G::BLOCK);
     for (int w = tid; w < NW; w += G::BLOCK) {
         sm.Fz[w] = a.frozen_words[w];
         sm.U[w] = 0u;
@@ -1392,6 +1426,10 @@ __device__ __forceinline__ void decode_codeword(const CwIO& a, int max_iter, flo
     if (tid == 0) {
         if (a.iters) *a.iters = iters;
         if (a.pe) *a.pe = (GSTOP || FREEZE) ? *sm.pe_acc() : (long long)iters * M * (N >> 1);
+    }
+    if constexpr (kChecked) {
+        group_sync<G::BLOCK, CPC>(grp);  // every store of this decode is done
+        redzones<M, false>(smem_raw, status, tid, G::BLOCK);
     }
 }
 

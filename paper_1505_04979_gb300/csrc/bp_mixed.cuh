@@ -28,7 +28,8 @@
 
 namespace polarbp {
 
-constexpr int kMixedSlice8 = 8800;  // bytes of shared memory per N = 256 group
+// bytes of shared memory per N = 256 group (the checked build's redzones need 11 x 256 more)
+constexpr int kMixedSlice8 = kChecked ? 8800 + 3072 : 8800;
 
 template <int MT, bool FREEZE>
 struct MixedTop {

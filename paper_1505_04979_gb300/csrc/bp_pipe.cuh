@@ -60,9 +60,22 @@ template <int M>
 struct PipeLayout {
     using L = SmemLayout<M>;
     static constexpr size_t off_hd1 = (L::bytes + 31) / 32 * 32;
-    static constexpr size_t off_ge1 = (off_hd1 + L::hd_bytes + 15) / 16 * 16;
-    static constexpr size_t bytes = (off_ge1 + 2 * sizeof(uint32_t) * Geo<M>::NW + 15) / 16 * 16;
+    static constexpr size_t end_hd1 = off_hd1 + L::hd_bytes;
+    static constexpr size_t off_ge1 = (end_hd1 + L::RZ + 15) / 16 * 16;
+    static constexpr size_t end_ge1 = off_ge1 + 2 * sizeof(uint32_t) * Geo<M>::NW;
+    static constexpr size_t bytes = (end_ge1 + L::RZ + 15) / 16 * 16;
 };
+
+// Fill (FILL) or compare every redzone of a PipeLayout<M> at base.
+template <int M, bool FILL>
+__device__ __forceinline__ void pipe_redzones(unsigned char* base, unsigned int* status, int tid, int stride)
+{
+    if constexpr (kChecked) {
+        redzones<M, FILL>(base, status, tid, stride);
+        redzone_pass<FILL>(base, PipeLayout<M>::end_hd1, kLayoutPipe, 0, status, tid, stride);
+        redzone_pass<FILL>(base, PipeLayout<M>::end_ge1, kLayoutPipe, 1, status, tid, stride);
+    }
+}
 
 template <int M>
 __device__ __forceinline__ void pipe_buffers(Smem<M>& sm, unsigned char* base, int it)
@@ -449,6 +462,7 @@ __device__ __forceinline__ void decode_pipe_codeword(const CwIO& a, int max_iter
     const int tid = threadIdx.x;
     Smem<M> sm(smem_raw);
 
+    pipe_redzones<M, true>(smem_raw, status, tid, THREADS);
     for (int w = tid; w < NW; w += THREADS) {
         sm.Fz[w] = a.frozen_words[w];
         sm.U[w] = 0u;
@@ -537,6 +551,10 @@ __device__ __forceinline__ void decode_pipe_codeword(const CwIO& a, int max_iter
     if (tid == 0) {
         if (a.iters) *a.iters = iters;
         if (a.pe) *a.pe = *sm.pe_acc();
+    }
+    if constexpr (kChecked) {
+        __syncthreads();  // every store of this decode is done
+        pipe_redzones<M, false>(smem_raw, status, tid, THREADS);
     }
 }
 

@@ -538,8 +538,9 @@ int polarbp_construct(int N, int K, const uint8_t* frozen_mask, double z0, polar
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_frozen, nw * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_frozen, words.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned int));
+    // status words: flags, then the checked build's redzone record
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, polarbp::kStatusWords * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, polarbp::kStatusWords * sizeof(unsigned int));
     for (int i = 0; i < kPipe && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&c->pipe[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->pipe_done[i], cudaEventDisableTiming);
@@ -982,17 +983,24 @@ int polarbp_get_status(const polarbp_code* c, void* stream)
 {
     if (!c) return fail(POLARBP_ERR_ARG, "code handle is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned int h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof h, cudaMemcpyDeviceToHost, s);
+    unsigned int h[polarbp::kStatusWords] = {};
+    cudaError_t e = cudaMemcpyAsync(h, c->d_status, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof h, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "get_status");
-    if (h & 1u) return fail(POLARBP_ERR_NONFINITE, "a decode saw a non-finite channel LLR");
+    if (h[0] & polarbp::kStatusRedzone) {
+        static const char* const layouts[] = {"?", "SmemLayout", "PipeLayout", "CLayout"};
+        const unsigned lay = h[2] >> 8;
+        return fail(POLARBP_ERR_CHECK, std::to_string(h[1]) + " redzone words changed; first in " +
+                                           layouts[lay < 4 ? lay : 0] + " redzone " + std::to_string(h[2] & 0xffu) +
+                                           " at byte " + std::to_string(h[3]));
+    }
+    if (h[0] & 1u) return fail(POLARBP_ERR_NONFINITE, "a decode saw a non-finite channel LLR");
     return POLARBP_OK;
 }
 
 const char* polarbp_last_error(void) { return g_last_error.c_str(); }
 
-const char* polarbp_version(void) { return "polarbp 0.1 (sm_103a)"; }
+const char* polarbp_version(void) { return polarbp::kChecked ? "polarbp 0.1 (sm_103a) checked" : "polarbp 0.1 (sm_103a)"; }
 
 }  // extern "C"
