@@ -313,11 +313,12 @@ int polarbp_awgn(const polarbp_code* code, uint64_t seed, uint64_t first_codewor
  * device address (cudaGetSymbolAddress) with that device current and keeps it
  * for the life of the process; make that first call before any stream capture.
  * cudaDeviceReset invalidates that address together with every code handle of
- * the device: after a reset, call nothing in this library on that device.  All calls share the one array and leave the
- * last call's contents in it; nothing in it needs to start at zero (each call
- * writes every byte it reads).  Calls that overlap on the GPU -- on different
- * streams or host threads at the same time on the same device -- race on the
- * array: serialise them.  Synchronises `stream` before returning.
+ * the device: after a reset, call nothing in this library on that device.  All
+ * calls share the one array and leave the last call's contents in it; nothing
+ * in it needs to start at zero (each call writes every byte it reads).  Calls
+ * that overlap on the GPU -- on different streams or host threads at the same
+ * time on the same device -- race on the array: serialise them.  Synchronises
+ * `stream` before returning.
  */
 #define POLARBP_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int polarbp_decode_host_noalloc(const polarbp_code* code, const float* llr, int batch, int max_iter, float scale,
