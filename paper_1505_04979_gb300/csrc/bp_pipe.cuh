@@ -571,8 +571,10 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
 }
 
 // The per-codeword decode as one out-of-line function, for the persistent kernels:
-// a loop around the inlined body compiles to code 9 % slower than one block per
-// codeword (more instructions, more instruction-fetch stalls); called, 2 %.
+// at N = 1024 a loop around the inlined body compiles to code 9 % slower than one
+// block per codeword (more instructions, more instruction-fetch stalls); called,
+// 2 %.  At N = 4096 the inlined loop is the faster of the two (26.8 against 27.3 ms
+// per 16,384 codewords at 2.5 dB), so the persistent kernel inlines it there.
 template <int M, bool GSTOP>
 __device__ __noinline__ void decode_pipe_codeword_call(const CwIO a, int max_iter, float alpha, unsigned int* status,
                                                        unsigned char* smem_raw)
@@ -608,7 +610,8 @@ __global__ void __launch_bounds__(PipeGeo<M>::THREADS, PipeGeo<M>::MIN_BLOCKS) b
                       nullptr,
                       a.bitrev[sg]};
         __syncthreads();  // every thread has read the popped index before the decode reuses the slot
-        decode_pipe_codeword_call<M, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
+        if constexpr (M == 12) decode_pipe_codeword<M, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
+        else decode_pipe_codeword_call<M, GSTOP>(io, a.max_iter, a.alpha, a.status[sg], smem_raw);
     }
 }
 
