@@ -375,7 +375,10 @@ int polarbp_decode_segments(const polarbp_segment* segs, int nseg, int max_iter,
  * group of threads splits into two groups that take codewords of half that
  * length in the two halves of its shared memory, down to one warp per N = 256
  * codeword.  Codewords retire at their own stop, independently of the others.
- * The codewords-per-block setting of the codes is not used.  The call may be
+ * With freezing and N = 4096 the longest length, the block has one warp more and
+ * decodes the N = 4096 codewords pipelined (a checker warp beside the sweep);
+ * every other length runs in the block mapping.  The codewords-per-block and
+ * thread-mapping settings of the codes are not used.  The call may be
  * captured into a CUDA graph after one uncaptured call (the first call per
  * kernel sets attributes and queries occupancy).
  *   segs, nseg, max_iter, scale, stop_mode, freeze_mode: as polarbp_decode_segments
@@ -402,8 +405,8 @@ int polarbp_get_codewords_per_block(const polarbp_code* code, int* codewords_per
  * polarbp_decode_segments use for this code when freezing at N = 256 .. 4096.
  * The pipelined mapping holds one codeword per block: with codewords per block
  * above 1 the persistent launch takes the block mapping.  polarbp_decode_mixed
- * always takes the block mapping.  Errors: POLARBP_ERR_ARG (NULL handle, unknown
- * mapping). */
+ * does not use this setting (it fixes the mapping per length).  Errors:
+ * POLARBP_ERR_ARG (NULL handle, unknown mapping). */
 int polarbp_set_thread_mapping(polarbp_code* code, int mapping);
 int polarbp_get_thread_mapping(const polarbp_code* code, int* mapping);
 
@@ -413,7 +416,9 @@ int polarbp_get_thread_mapping(const polarbp_code* code, int* mapping);
  * codewords-per-block value with the given decode settings (the pipelined
  * mapping with one codeword per block, and the block mapping with 1, 2 or 4,
  * as the code length admits) and keep the fastest pair in the handle.
- * Allocates and frees temporary device memory; synchronises `stream`.
+ * Allocates and frees temporary device memory; synchronises `stream`.  The
+ * handle's settings change while it runs: decode nothing with this handle from
+ * another thread meanwhile.  On an error the previous settings are restored.
  * Errors: POLARBP_ERR_ARG (K = 0), POLARBP_ERR_UNSUPPORTED, POLARBP_ERR_NOMEM, POLARBP_ERR_CUDA.
  */
 int polarbp_autotune(polarbp_code* code, int max_iter, float scale, int stop_mode, int freeze_mode, void* stream);
